@@ -1,0 +1,184 @@
+/*
+ * sos_gb300.h -- C ABI of the GB300 engine for the over-parameterised
+ * sum-of-squares objective of Keren, Osadchy and Poranne (arXiv 2410.19844).
+ *
+ * Problem (Sec. 1.1, Eq. 1 and Eq. 2).  A polynomial p of degree <= 2d in n
+ * variables is a sum of squares iff p = m_d B m_d^T for a PSD matrix B, where
+ * m_d lists the monomials of degree <= d.  Writing B = A A^T with A of size
+ * N x r (N = C(n+d, d) monomials, r columns = r squares q_k), the engine
+ * minimises
+ *         loss(A) = 1/2 || c(A) - p ||^2 ,   c(A) = coefficients of sum_k q_k^2,
+ * over the M = C(n+2d, 2d) coefficients of degree <= 2d, with first-order
+ * steps (Adam, the paper's optimiser in Sec. 3, or plain gradient descent).
+ * The factor 1/2 is this library's convention; the paper's error (Eq. 2) is
+ * 2 * loss.  The gradient is grad = 2 H(c - p) A with H[a][b] = (c - p)[a+b].
+ *
+ * Monomial order (Sec. 1.1, the printed example (x1^2, x1x2, x2^2, x1, x2, 1)):
+ * higher total degree first, then lexicographically larger exponent tuple
+ * first (x1 compared first).  Rows of A, and entries of c and p, use it.
+ *
+ * Conventions for every entry point:
+ *  - Every function returns a sos_status; no C++ exception crosses the ABI.
+ *    On failure sos_last_error() returns a message (thread-local, valid until
+ *    the next call on the same thread).
+ *  - "dev" pointers are CUDA device pointers owned by the caller; "host"
+ *    pointers are host memory owned by the caller.  The library owns only the
+ *    plan (host tables and their device copies).
+ *  - Matrices are dense and row-major.  A has N rows (monomials of degree
+ *    <= d, in the order above) and r columns (squares).  p and c have M
+ *    entries.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    entry points are asynchronous on that stream unless stated otherwise.
+ *  - The first device call on a plan uploads its tables to the current
+ *    device synchronously; make it before capturing a stream into a graph.
+ *  - Element types follow `prec`: SOS_BF16 and SOS_FP32 take float A, p,
+ *    grad; SOS_FP64 takes double.  SOS_BF16 rounds A to bfloat16 for the two
+ *    contractions (tensor cores, FP32 accumulation); SOS_FP32 runs them on
+ *    CUDA cores in FP32 (no TF32); SOS_FP64 in FP64.  Losses are double.
+ */
+#ifndef SOS_GB300_H
+#define SOS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sos_plan_s* sos_plan_t;
+
+typedef enum {
+    SOS_OK = 0,
+    SOS_E_INVALID = -1,      /* bad argument, size or pointer */
+    SOS_E_CUDA = -2,         /* a CUDA runtime or driver call failed */
+    SOS_E_NOMEM = -3,        /* an allocation failed or a table is too large */
+    SOS_E_TIMEOUT = -4,      /* a bounded device wait gave up; the kernel returned */
+    SOS_E_NONFINITE = -5,    /* a NaN or Inf appeared in c, p or the residual */
+    SOS_E_UNSUPPORTED = -6   /* the request is valid but not implemented here */
+} sos_status;
+
+typedef enum { SOS_BF16 = 0, SOS_FP32 = 1, SOS_FP64 = 2 } sos_prec;
+typedef enum { SOS_ADAM = 0, SOS_GD = 1 } sos_opt;
+typedef enum {
+    SOS_VERDICT_ERROR = -1,
+    SOS_VERDICT_NOT_CONVERGED = 0,   /* a gradient method never proves "not SOS" */
+    SOS_VERDICT_SOS = 1              /* ||c(A) - p||_2 <= tol * ||p||_2 in FP64 */
+} sos_verdict;
+
+/* ---- plan (host only; no GPU needed) ---------------------------------- */
+
+/* Builds the monomial tables for polynomials of degree <= two_d in n
+ * variables with r squares (Sec. 1.1; the sizes follow from counting
+ * monomials, Sec. 1.1).  Requires n >= 1, two_d even >= 2, r >= 1,
+ * n + two_d <= 255.  The plan is host-side until its first device call.
+ * Errors: SOS_E_INVALID for bad sizes, SOS_E_NOMEM when the tables do not
+ * fit (M must stay below 2^31). */
+int sos_plan_create(int n, int two_d, int64_t r, sos_plan_t* out);
+
+/* Frees the plan, its host tables and (with its device current) its device
+ * tables.  NULL is accepted. */
+int sos_plan_destroy(sos_plan_t plan);
+
+/* N = C(n+d, d) rows of A, M = C(n+2d, 2d) coefficients, r columns. */
+int sos_plan_sizes(sos_plan_t plan, int64_t* N, int64_t* M, int64_t* r);
+
+/* Writes the exponent table, one row of n bytes per monomial, in the
+ * canonical order.  which = 0: the N monomials of degree <= d (host, N x n);
+ * which = 1: the M monomials of degree <= 2d (host, M x n). */
+int sos_plan_monomials(sos_plan_t plan, int which, uint8_t* exps);
+
+/* Writes idx[a*N + b] = position of x^a x^b among the M coefficients, the
+ * index table of the Gram identity (Eq. 1): c_g = sum_{a+b=g} (A A^T)_ab.
+ * host N x N int32.  SOS_E_NOMEM if N*N exceeds 2^31 entries. */
+int sos_plan_idx(sos_plan_t plan, int32_t* idx);
+
+/* Bytes of device workspace that sos_coeffs / sos_loss_grad / sos_step need
+ * for this plan and precision.  Callers allocate it (any 256-byte aligned
+ * device buffer), initialise it once with sos_workspace_init, and pass it in. */
+int sos_workspace_size(sos_plan_t plan, int prec, size_t* bytes);
+
+/* Zeroes the workspace's status word and reduction counters (its first 256
+ * bytes).  Call once after allocating a workspace, before its first use;
+ * later calls keep it consistent themselves.  Asynchronous on `stream`. */
+int sos_workspace_init(sos_plan_t plan, int prec, void* workspace, void* stream);
+
+/* ---- one pass of the objective (device, asynchronous) ------------------ */
+
+/* c(A) = coefficients of sum_k q_k^2 (Eq. 1 with B = A A^T).
+ * A: dev N x r; c: dev M (float for BF16/FP32, double for FP64). */
+int sos_coeffs(sos_plan_t plan, int prec, const void* A, void* c,
+               void* workspace, void* stream);
+
+/* loss = 1/2 ||c(A) - p||^2 (Eq. 2) and its gradient 2 H(c - p) A.
+ * A: dev N x r; p: dev M; grad: dev N x r, or NULL for the loss only;
+ * loss: dev double[2] = {loss, ||p||^2}.  A NaN or Inf in c or p is
+ * reported through sos_read_status() after the stream completes. */
+int sos_loss_grad(sos_plan_t plan, int prec, const void* A, const void* p,
+                  void* grad, void* loss, void* workspace, void* stream);
+
+/* The same pass for `batch` independent problems of one plan, FP32 or FP64
+ * on CUDA cores (one launch per kernel for the whole batch).  A and grad:
+ * dev batch x N x r; p: dev batch x M; loss: dev double[batch][2].  The
+ * workspace comes from sos_workspace_size_batched. */
+int sos_workspace_size_batched(sos_plan_t plan, int prec, int64_t batch, size_t* bytes);
+int sos_loss_grad_batched(sos_plan_t plan, int prec, int64_t batch, const void* A,
+                          const void* p, void* grad, void* loss, void* workspace,
+                          void* stream);
+
+/* Optimiser settings (Sec. 3: "basic ADAM"; the paper gives no constants,
+ * these default to Kingma and Ba's: beta1 0.9, beta2 0.999, eps 1e-8). */
+typedef struct {
+    int optimizer;      /* sos_opt */
+    double lr;
+    double beta1, beta2, eps;
+} sos_step_opts;
+
+/* Optimiser state, all dev, caller-owned: A (N x r) updated in place; m and
+ * v (N x r, zero before the first Adam step; unused by GD); t = number of
+ * steps already taken (incremented by sos_step). */
+typedef struct {
+    void* A;
+    void* m;
+    void* v;
+    int64_t t;
+} sos_state;
+
+/* One iteration: loss and gradient at A, then the update of A (and m, v).
+ * loss: dev double[2] = {loss before the update, ||p||^2}, or NULL. */
+int sos_step(sos_plan_t plan, int prec, sos_state* state, const void* p,
+             const sos_step_opts* opts, void* loss, void* workspace, void* stream);
+
+/* Returns the status word the last device pass left in the workspace
+ * (SOS_OK, SOS_E_NONFINITE or SOS_E_TIMEOUT).  Synchronises `stream`. */
+int sos_read_status(sos_plan_t plan, int prec, void* workspace, void* stream);
+
+/* ---- certificate (synchronous) ------------------------------------------ */
+
+/* FP64 certificate (Sec. 3: the error norm is about 1e-8 of the norm of the
+ * coefficient vector for SOS inputs): evaluates c(A) in FP64 (A promoted),
+ * rel = ||c(A) - p||_2 / ||p||_2, verdict = SOS if rel <= tol_rel.
+ * A: dev N x r, float (a_is_double = 0) or double (1); p: dev M double.
+ * rel_out, verdict_out: host.  `workspace` is unused (pass NULL): the call
+ * allocates and frees its own FP64 scratch and synchronises `stream`. */
+int sos_certify(sos_plan_t plan, const void* A, int a_is_double, const double* p,
+                double tol_rel, double* rel_out, int* verdict_out,
+                void* workspace, void* stream);
+
+/* Diagnostic: a plain tcgen05 BF16 GEMM with FP32 output through the same
+ * tile machinery as the two contractions.  D (dev m x n, row stride n) =
+ * X (dev m x k bf16, row stride ldx) times Y^T (b_mn_major = 0: Y is n x k,
+ * row stride ldy) or times Y (b_mn_major = 1: Y is k x n, row stride ldy).
+ * Row strides must be multiples of 8 elements and the bases 16-byte
+ * aligned.  status: dev int32, zero on entry; a timed-out wait sets it.
+ * Synchronises `stream`. */
+int sos_diag_gemm_bf16(int b_mn_major, const void* X, const void* Y, float* D,
+                       int64_t m, int64_t n, int64_t k, int64_t ldx, int64_t ldy,
+                       int32_t* status, void* stream);
+
+const char* sos_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOS_GB300_H */

@@ -1,0 +1,176 @@
+"""ctypes binding of ``libsos_gb300.so``: the C ABI of ``include/sos_gb300.h``
+under the same names, argument marshalling only.  Every computation runs in
+the library; a missing library raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SOS_OK = 0
+SOS_E_INVALID = -1
+SOS_E_CUDA = -2
+SOS_E_NOMEM = -3
+SOS_E_TIMEOUT = -4
+SOS_E_NONFINITE = -5
+SOS_E_UNSUPPORTED = -6
+
+SOS_BF16, SOS_FP32, SOS_FP64 = 0, 1, 2
+SOS_ADAM, SOS_GD = 0, 1
+SOS_VERDICT_ERROR, SOS_VERDICT_NOT_CONVERGED, SOS_VERDICT_SOS = -1, 0, 1
+
+PREC = {"bf16": SOS_BF16, "fp32": SOS_FP32, "fp64": SOS_FP64}
+
+EXPORTS = [
+    "sos_plan_create", "sos_plan_destroy", "sos_plan_sizes", "sos_plan_monomials", "sos_plan_idx",
+    "sos_workspace_size", "sos_workspace_init", "sos_coeffs", "sos_loss_grad",
+    "sos_workspace_size_batched", "sos_loss_grad_batched", "sos_step", "sos_read_status",
+    "sos_certify", "sos_diag_gemm_bf16", "sos_last_error",
+]
+
+
+class SOSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class sos_step_opts(ctypes.Structure):
+    _fields_ = [("optimizer", ctypes.c_int), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class sos_state(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("t", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(auto_build: bool = True):
+    """The loaded library; builds it in-tree first when missing or stale."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if auto_build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library missing at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "sos_plan_create": [i32, i32, i64, P(vp)],
+        "sos_plan_destroy": [vp],
+        "sos_plan_sizes": [vp, P(i64), P(i64), P(i64)],
+        "sos_plan_monomials": [vp, i32, vp],
+        "sos_plan_idx": [vp, vp],
+        "sos_workspace_size": [vp, i32, P(ctypes.c_size_t)],
+        "sos_workspace_init": [vp, i32, vp, vp],
+        "sos_coeffs": [vp, i32, vp, vp, vp, vp],
+        "sos_loss_grad": [vp, i32, vp, vp, vp, vp, vp, vp],
+        "sos_workspace_size_batched": [vp, i32, i64, P(ctypes.c_size_t)],
+        "sos_loss_grad_batched": [vp, i32, i64, vp, vp, vp, vp, vp, vp],
+        "sos_step": [vp, i32, P(sos_state), vp, P(sos_step_opts), vp, vp, vp],
+        "sos_read_status": [vp, i32, vp, vp],
+        "sos_certify": [vp, vp, i32, vp, dbl, P(dbl), P(i32), vp, vp],
+        "sos_diag_gemm_bf16": [i32, vp, vp, vp, i64, i64, i64, i64, i64, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i32
+    L.sos_last_error.argtypes = []
+    L.sos_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> int:
+    if rc != SOS_OK:
+        raise SOSError(rc, lib().sos_last_error().decode(errors="replace"))
+    return rc
+
+
+# ---- same-named wrappers ---------------------------------------------------------
+
+def sos_plan_create(n: int, two_d: int, r: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sos_plan_create(n, two_d, r, ctypes.byref(h)))
+    return h.value
+
+
+def sos_plan_destroy(plan: int) -> None:
+    _check(lib().sos_plan_destroy(plan))
+
+
+def sos_plan_sizes(plan: int):
+    N, M, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sos_plan_sizes(plan, ctypes.byref(N), ctypes.byref(M), ctypes.byref(r)))
+    return N.value, M.value, r.value
+
+
+def sos_plan_monomials(plan: int, which: int, out_ptr: int) -> None:
+    _check(lib().sos_plan_monomials(plan, which, out_ptr))
+
+
+def sos_plan_idx(plan: int, out_ptr: int) -> None:
+    _check(lib().sos_plan_idx(plan, out_ptr))
+
+
+def sos_workspace_size(plan: int, prec: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sos_workspace_size(plan, prec, ctypes.byref(b)))
+    return b.value
+
+
+def sos_workspace_init(plan: int, prec: int, ws: int, stream: int) -> None:
+    _check(lib().sos_workspace_init(plan, prec, ws, stream))
+
+
+def sos_coeffs(plan, prec, A, c, ws, stream) -> None:
+    _check(lib().sos_coeffs(plan, prec, A, c, ws, stream))
+
+
+def sos_loss_grad(plan, prec, A, p, grad, loss, ws, stream) -> None:
+    _check(lib().sos_loss_grad(plan, prec, A, p, grad, loss, ws, stream))
+
+
+def sos_workspace_size_batched(plan: int, prec: int, batch: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sos_workspace_size_batched(plan, prec, batch, ctypes.byref(b)))
+    return b.value
+
+
+def sos_loss_grad_batched(plan, prec, batch, A, p, grad, loss, ws, stream) -> None:
+    _check(lib().sos_loss_grad_batched(plan, prec, batch, A, p, grad, loss, ws, stream))
+
+
+def sos_step(plan, prec, state: sos_state, p, opts: sos_step_opts, loss, ws, stream) -> None:
+    _check(lib().sos_step(plan, prec, ctypes.byref(state), p, ctypes.byref(opts), loss, ws, stream))
+
+
+def sos_read_status(plan, prec, ws, stream) -> int:
+    """Returns the status code (does not raise) and clears it."""
+    return int(lib().sos_read_status(plan, prec, ws, stream))
+
+
+def sos_certify(plan, A, a_is_double, p64, tol_rel, stream):
+    rel, verdict = ctypes.c_double(), ctypes.c_int()
+    _check(lib().sos_certify(plan, A, int(a_is_double), p64, tol_rel, ctypes.byref(rel),
+                             ctypes.byref(verdict), None, stream))
+    return rel.value, verdict.value
+
+
+def sos_diag_gemm_bf16(b_mn_major, X, Y, D, m, n, k, ldx, ldy, status, stream) -> None:
+    _check(lib().sos_diag_gemm_bf16(int(b_mn_major), X, Y, D, m, n, k, ldx, ldy, status, stream))
+
+
+def sos_last_error() -> str:
+    return lib().sos_last_error().decode(errors="replace")

@@ -1,0 +1,113 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/sos_gb300.h"
+
+namespace sos {
+
+// ---- error state ---------------------------------------------------------
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SOS_CUDA(...)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (__VA_ARGS__);                                 \
+        if (e_ != cudaSuccess) return ::sos::cuda_fail(e_, #__VA_ARGS__); \
+    } while (0)
+
+#define SOS_CHECK(...)                  \
+    do {                                \
+        int s_ = (__VA_ARGS__);         \
+        if (s_ != SOS_OK) return s_;    \
+    } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+// ---- workspace -----------------------------------------------------------
+
+constexpr int kResidBlocks = 512;     // blocks of the residual reduction
+
+struct Workspace {
+    size_t status = 0;     // int32[64]: [0] status word, [1..] reduction counters
+    size_t partials = 0;   // double[2 * kResidBlocks]
+    size_t loss = 0;       // double[2] when the caller passes no loss buffer
+    size_t c = 0;          // M accumulators (float or double)
+    size_t resid = 0;      // M residuals (float or double)
+    size_t grad = 0;       // N x r gradient (float or double)
+    size_t a16 = 0;        // N x ld16 bf16 copy of A   (SOS_BF16 only)
+    size_t h16 = 0;        // N x ld16h bf16 H(resid)   (SOS_BF16 only)
+    size_t total = 0;
+};
+
+// ---- plan ----------------------------------------------------------------
+
+struct DeviceTables {
+    int device = -1;
+    int num_sms = 0;
+    int32_t* idx = nullptr;     // N x ld_idx, idx[a][b] = rank of x^a x^b
+    int2* fwd_tiles = nullptr;  // (I, J) tiles of the upper triangle of A A^T
+    int2* adj_tiles = nullptr;  // (alpha block, column block) tiles of 2 H A
+    int num_fwd_tiles = 0;
+    int num_adj_tiles = 0;
+};
+
+}  // namespace sos
+
+struct sos_plan_s {
+    int n = 0, two_d = 0, d = 0;
+    int64_t N = 0, M = 0, r = 0;
+    int64_t ld_idx = 0;   // row stride of the device idx table (multiple of 8)
+    int64_t ld16 = 0;     // row stride of the bf16 copy of A (multiple of 64)
+    int64_t ld16h = 0;    // row stride of the bf16 H (multiple of 64)
+    std::vector<uint8_t> Ed, E2d;   // exponent tables, canonical order
+    std::vector<uint8_t> Sd;        // suffix sums S_j(a) of the rows of Ed, N x n
+    std::vector<int32_t> phi;       // n x (2d+1): rank(g) = sum_j phi[j][S_j(g)]
+    sos::DeviceTables dev;
+    std::mutex mu;
+};
+
+namespace sos {
+
+Workspace workspace_layout(const sos_plan_s* plan, int prec);
+int ensure_device(sos_plan_s* plan);
+
+// ---- kernel launchers (kernels_simt.cu) ------------------------------------
+
+int launch_build_idx(const sos_plan_s* plan, int32_t* idx, const uint8_t* d_S, const int32_t* d_phi,
+                     cudaStream_t st);
+int launch_cast_bf16(const float* A, int64_t N, int64_t r, void* a16, int64_t ld16,
+                     cudaStream_t st);
+template <typename Tin, typename Tacc>
+int launch_simt_forward(const sos_plan_s* plan, const Tin* A, Tacc* c, int64_t batch,
+                        cudaStream_t st);
+template <typename T>
+int launch_residual(const sos_plan_s* plan, const T* c, const T* p, T* resid, double* loss,
+                    double* partials, int32_t* status, int64_t batch, cudaStream_t st);
+template <typename T>
+int launch_simt_adjoint(const sos_plan_s* plan, const T* A, const T* resid, T* grad,
+                        int64_t batch, cudaStream_t st);
+int launch_build_h16(const sos_plan_s* plan, const float* resid, void* h16, cudaStream_t st);
+template <typename T>
+int launch_update(int64_t N, int64_t r, T* A, T* m, T* v, const T* grad, int optimizer,
+                  int64_t t, double lr, double b1, double b2, double eps, void* a16,
+                  int64_t ld16, cudaStream_t st);
+template <typename T>
+int launch_fill(T* x, int64_t count, T value, cudaStream_t st);
+
+// ---- tensor-core kernels (kernels_tc.cu) ------------------------------------
+
+int launch_tc_forward(const sos_plan_s* plan, const void* a16, float* c, int32_t* status,
+                      cudaStream_t st);
+int launch_tc_adjoint(const sos_plan_s* plan, const void* h16, const void* a16, float* grad,
+                      int32_t* status, cudaStream_t st);
+
+}  // namespace sos

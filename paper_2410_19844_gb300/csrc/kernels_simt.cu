@@ -1,0 +1,440 @@
+// CUDA-core kernels: plan tables, casts, the FP32/FP64 forward and adjoint,
+// the residual/loss reduction and the optimiser update.
+//
+//   forward   c_g = sum_{a+b=g} w_ab (A A^T)_ab, w = 1 on the diagonal, 2 above
+//             (Eq. 1 with B = A A^T; each unordered pair counted once)
+//   residual  r = c - p, loss = 1/2 ||r||^2, ||p||^2         (Eq. 2)
+//   adjoint   grad = 2 H(r) A, H[a][b] = r[idx(a, b)]        (chain rule of Eq. 2)
+//   update    gradient descent or Adam (Sec. 3)
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace sos {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+template <typename T>
+__device__ __forceinline__ bool finite_val(T x) {
+    return isfinite(x);
+}
+
+// ---- idx table ----------------------------------------------------------------
+
+__global__ void build_idx_kernel(int n, int W, int64_t N, int64_t ld, const uint8_t* __restrict__ S,
+                                 const int32_t* __restrict__ phi, int32_t* __restrict__ idx) {
+    extern __shared__ int32_t sphi[];
+    for (int i = threadIdx.x; i < n * W; i += blockDim.x) sphi[i] = phi[i];
+    __syncthreads();
+    for (int64_t a = blockIdx.y; a < N; a += gridDim.y) {
+        const uint8_t* Sa = S + a * n;
+        for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < ld;
+             b += (int64_t)gridDim.x * blockDim.x) {
+            int32_t g = 0;
+            if (b < N) {
+                const uint8_t* Sb = S + b * n;
+                for (int j = 0; j < n; ++j) g += sphi[j * W + Sa[j] + Sb[j]];
+            }
+            idx[a * ld + b] = g;
+        }
+    }
+}
+
+// ---- bf16 copy of A -------------------------------------------------------------
+
+__global__ void cast_bf16_kernel(const float* __restrict__ A, int64_t N, int64_t r,
+                                 __nv_bfloat16* __restrict__ a16, int64_t ld) {
+    const int64_t total = N * r;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / r, col = i - row * r;
+        a16[row * ld + col] = __float2bfloat16_rn(A[i]);
+    }
+}
+
+// ---- forward: upper-triangle tiles of A A^T, segment-summed into c ------------------
+// 64 x 64 tile (I, J), J >= I; 256 threads, 4 x 4 outputs each at rows
+// ty + 16 i and columns tx + 16 j; K in chunks of 16 staged in shared memory.
+
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(kThreads)
+simt_forward_kernel(const Tin* __restrict__ A, int64_t N, int64_t r, const int32_t* __restrict__ idx,
+                    int64_t ld_idx, Tacc* __restrict__ c, int64_t strideA, int64_t strideC) {
+    const int I = blockIdx.y, J = blockIdx.x;
+    if (J < I) return;
+    A += (int64_t)blockIdx.z * strideA;
+    c += (int64_t)blockIdx.z * strideC;
+    __shared__ Tacc As[16][64];
+    __shared__ Tacc Bs[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)I * 64, col0 = (int64_t)J * 64;
+    Tacc acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = Tacc(0);
+    for (int64_t k0 = 0; k0 < r; k0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = tid + l * kThreads, rr = e >> 4, kk = e & 15;
+            const int64_t gk = k0 + kk, ga = row0 + rr, gb = col0 + rr;
+            As[kk][rr] = (ga < N && gk < r) ? (Tacc)A[ga * r + gk] : Tacc(0);
+            Bs[kk][rr] = (gb < N && gk < r) ? (Tacc)A[gb * r + gk] : Tacc(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            Tacc a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t a = row0 + ty + 16 * i;
+        if (a >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t b = col0 + tx + 16 * j;
+            if (b < N && b >= a) {
+                const Tacc w = (b == a) ? Tacc(1) : Tacc(2);
+                atomicAdd(&c[idx[a * ld_idx + b]], w * acc[i][j]);
+            }
+        }
+    }
+}
+
+// ---- residual and loss ----------------------------------------------------------
+// grid.y = instance.  With one block per instance the block reduces alone;
+// with several, the last block to finish (ticket counter) sums the per-block
+// partials in block order, so the result does not depend on timing.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+residual_kernel(const T* __restrict__ c, const T* __restrict__ p, T* __restrict__ resid, int64_t M,
+                double* __restrict__ loss, double* __restrict__ partials, int32_t* __restrict__ status,
+                int32_t* __restrict__ counter) {
+    const int64_t inst = blockIdx.y;
+    c += inst * M;
+    p += inst * M;
+    if (resid) resid += inst * M;
+    loss += inst * 2;
+    partials += inst * 2 * gridDim.x;
+    double sr = 0.0, sp = 0.0;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const T cv = c[i], pv = p[i];
+        const T e = cv - pv;
+        if (resid) resid[i] = e;
+        if (!finite_val(cv) || !finite_val(pv) || !finite_val(e)) bad = 1;
+        sr += (double)e * (double)e;
+        sp += (double)pv * (double)pv;
+    }
+    __shared__ double red_r[kThreads / 32], red_p[kThreads / 32];
+    __shared__ int red_bad;
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) red_bad = 0;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, o);
+        sp += __shfl_down_sync(0xffffffffu, sp, o);
+    }
+    if (bad) red_bad = 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red_r[warp] = sr;
+        red_p[warp] = sp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, tp = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            tr += red_r[w];
+            tp += red_p[w];
+        }
+        if (red_bad) set_status(status, SOS_E_NONFINITE);
+        if (gridDim.x == 1) {
+            loss[0] = 0.5 * tr;
+            loss[1] = tp;
+            is_last = false;
+        } else {
+            partials[2 * blockIdx.x] = tr;
+            partials[2 * blockIdx.x + 1] = tp;
+            __threadfence();
+            const int ticket = atomicAdd(counter + inst, 1);
+            is_last = (ticket == (int)gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        __threadfence();
+        double tr = 0.0, tp = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            tr += ((volatile double*)partials)[2 * b];
+            tp += ((volatile double*)partials)[2 * b + 1];
+        }
+        loss[0] = 0.5 * tr;
+        loss[1] = tp;
+        counter[inst] = 0;
+    }
+}
+
+// ---- adjoint on CUDA cores: grad = 2 H(r) A, H gathered from r in the loader ----------
+// Output tile 64 (rows a) x 64 (columns k); the contraction runs over b in
+// chunks of 16.  H[a][b] = r[idx[a][b]] is read straight from the residual
+// while staging, so H is never stored.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const int32_t* __restrict__ idx,
+                    int64_t ld_idx, int64_t N, int64_t r, T* __restrict__ grad, int64_t strideA,
+                    int64_t strideR) {
+    A += (int64_t)blockIdx.z * strideA;
+    grad += (int64_t)blockIdx.z * strideA;
+    resid += (int64_t)blockIdx.z * strideR;
+    __shared__ T Hs[16][64];
+    __shared__ T Bs[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.y * 64, col0 = (int64_t)blockIdx.x * 64;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int64_t b0 = 0; b0 < N; b0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = tid + l * kThreads;
+            {   // H tile: 64 rows a x 16 columns b
+                const int rr = e >> 4, kk = e & 15;
+                const int64_t a = row0 + rr, b = b0 + kk;
+                Hs[kk][rr] = (a < N && b < N) ? resid[idx[a * ld_idx + b]] : T(0);
+            }
+            {   // A tile: 16 rows b x 64 columns k
+                const int kk = e >> 6, cc = e & 63;
+                const int64_t b = b0 + kk, k = col0 + cc;
+                Bs[kk][cc] = (b < N && k < r) ? A[b * r + k] : T(0);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Hs[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t a = row0 + ty + 16 * i;
+        if (a >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t k = col0 + tx + 16 * j;
+            if (k < r) grad[a * r + k] = T(2) * acc[i][j];
+        }
+    }
+}
+
+// ---- H(r) in bf16 for the tensor-core adjoint ----------------------------------------
+// Each thread writes 8 consecutive b of one row a with one 16-byte store.
+
+__global__ void build_h16_kernel(const float* __restrict__ resid, const int32_t* __restrict__ idx,
+                                 int64_t ld_idx, int64_t N, __nv_bfloat16* __restrict__ h, int64_t ldh) {
+    const int64_t chunks = (N + 7) / 8;
+    const int64_t total = N * chunks;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = i / chunks, b0 = (i - a * chunks) * 8;
+        const int32_t* irow = idx + a * ld_idx + b0;
+        __nv_bfloat16* hrow = h + a * ldh + b0;
+        if (b0 + 8 <= N) {
+            const int4 i0 = *reinterpret_cast<const int4*>(irow);
+            const int4 i1 = *reinterpret_cast<const int4*>(irow + 4);
+            __nv_bfloat162 v0 = __floats2bfloat162_rn(resid[i0.x], resid[i0.y]);
+            __nv_bfloat162 v1 = __floats2bfloat162_rn(resid[i0.z], resid[i0.w]);
+            __nv_bfloat162 v2 = __floats2bfloat162_rn(resid[i1.x], resid[i1.y]);
+            __nv_bfloat162 v3 = __floats2bfloat162_rn(resid[i1.z], resid[i1.w]);
+            uint4 out;
+            out.x = *reinterpret_cast<uint32_t*>(&v0);
+            out.y = *reinterpret_cast<uint32_t*>(&v1);
+            out.z = *reinterpret_cast<uint32_t*>(&v2);
+            out.w = *reinterpret_cast<uint32_t*>(&v3);
+            *reinterpret_cast<uint4*>(hrow) = out;
+        } else {
+            for (int64_t b = b0; b < N; ++b) hrow[b - b0] = __float2bfloat16_rn(resid[irow[b - b0]]);
+        }
+    }
+}
+
+// ---- optimiser update ---------------------------------------------------------------
+
+template <typename T>
+__global__ void update_kernel(int64_t N, int64_t r, T* __restrict__ A, T* __restrict__ m,
+                              T* __restrict__ v, const T* __restrict__ g, int optimizer, T lr, T b1,
+                              T b2, T eps, T c1, T c2, __nv_bfloat16* __restrict__ a16, int64_t ld16) {
+    const int64_t total = N * r;
+    const T one = T(1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const T gi = g[i];
+        T a = A[i];
+        if (optimizer == SOS_GD) {
+            a -= lr * gi;
+        } else {
+            const T mi = b1 * m[i] + (one - b1) * gi;
+            const T vi = b2 * v[i] + (one - b2) * gi * gi;
+            m[i] = mi;
+            v[i] = vi;
+            const T mhat = mi / c1;
+            const T vhat = vi / c2;
+            a -= lr * mhat / (sqrt(vhat) + eps);
+        }
+        A[i] = a;
+        if (a16) {
+            const int64_t row = i / r, col = i - row * r;
+            a16[row * ld16 + col] = __float2bfloat16_rn((float)a);
+        }
+    }
+}
+
+template <typename T>
+__global__ void fill_kernel(T* x, int64_t count, T value) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = value;
+}
+
+int grid_for(int64_t work, int cap = 152 * 16) {
+    int64_t g = (work + kThreads - 1) / kThreads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+// ---- launchers ---------------------------------------------------------------------
+
+int launch_build_idx(const sos_plan_s* p, int32_t* idx, const uint8_t* d_S, const int32_t* d_phi,
+                     cudaStream_t st) {
+    const int W = p->two_d + 1;
+    const size_t smem = (size_t)p->n * W * sizeof(int32_t);
+    if (smem > 48 * 1024) return fail(SOS_E_UNSUPPORTED, "build_idx: n * (2d+1) too large");
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(p->ld_idx, kThreads), 64),
+              (unsigned)std::min<int64_t>(p->N, 65535));
+    build_idx_kernel<<<grid, kThreads, smem, st>>>(p->n, W, p->N, p->ld_idx, d_S, d_phi, idx);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+int launch_cast_bf16(const float* A, int64_t N, int64_t r, void* a16, int64_t ld16, cudaStream_t st) {
+    cast_bf16_kernel<<<grid_for(N * r), kThreads, 0, st>>>(A, N, r, (__nv_bfloat16*)a16, ld16);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+template <typename Tin, typename Tacc>
+int launch_simt_forward(const sos_plan_s* p, const Tin* A, Tacc* c, int64_t batch, cudaStream_t st) {
+    const int64_t T = ceil_div(p->N, 64);
+    if (T > 65535 || batch > 65535) return fail(SOS_E_UNSUPPORTED, "simt_forward: too many tiles");
+    dim3 grid((unsigned)T, (unsigned)T, (unsigned)batch);
+    simt_forward_kernel<Tin, Tacc><<<grid, kThreads, 0, st>>>(A, p->N, p->r, p->dev.idx, p->ld_idx, c,
+                                                              p->N * p->r, p->M);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+template <typename T>
+int launch_residual(const sos_plan_s* p, const T* c, const T* pv, T* resid, double* loss,
+                    double* partials, int32_t* status, int64_t batch, cudaStream_t st) {
+    if (batch > 65535) return fail(SOS_E_UNSUPPORTED, "residual: batch too large");
+    int blocks = 1;
+    if (batch == 1) blocks = (int)std::min<int64_t>(kResidBlocks, std::max<int64_t>(1, ceil_div(p->M, 4 * kThreads)));
+    dim3 grid(blocks, (unsigned)batch);
+    residual_kernel<T><<<grid, kThreads, 0, st>>>(c, pv, resid, p->M, loss, partials, status, status + 1);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+template <typename T>
+int launch_simt_adjoint(const sos_plan_s* p, const T* A, const T* resid, T* grad, int64_t batch,
+                        cudaStream_t st) {
+    const int64_t TI = ceil_div(p->N, 64), TK = ceil_div(p->r, 64);
+    if (TI > 65535 || batch > 65535 || TK > INT32_MAX) return fail(SOS_E_UNSUPPORTED, "simt_adjoint: too many tiles");
+    dim3 grid((unsigned)TK, (unsigned)TI, (unsigned)batch);
+    simt_adjoint_kernel<T><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r, grad,
+                                                      p->N * p->r, p->M);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+int launch_build_h16(const sos_plan_s* p, const float* resid, void* h16, cudaStream_t st) {
+    const int64_t work = p->N * ceil_div(p->N, 8);
+    build_h16_kernel<<<grid_for(work, p->dev.num_sms * 8), kThreads, 0, st>>>(
+        resid, p->dev.idx, p->ld_idx, p->N, (__nv_bfloat16*)h16, p->ld16h);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+template <typename T>
+int launch_update(int64_t N, int64_t r, T* A, T* m, T* v, const T* grad, int optimizer, int64_t t,
+                  double lr, double b1, double b2, double eps, void* a16, int64_t ld16, cudaStream_t st) {
+    const double c1 = 1.0 - std::pow(b1, (double)t);
+    const double c2 = 1.0 - std::pow(b2, (double)t);
+    update_kernel<T><<<grid_for(N * r), kThreads, 0, st>>>(N, r, A, m, v, grad, optimizer, (T)lr, (T)b1,
+                                                           (T)b2, (T)eps, (T)c1, (T)c2,
+                                                           (__nv_bfloat16*)a16, ld16);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+template <typename T>
+int launch_fill(T* x, int64_t count, T value, cudaStream_t st) {
+    fill_kernel<T><<<grid_for(count), kThreads, 0, st>>>(x, count, value);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+template int launch_simt_forward<float, float>(const sos_plan_s*, const float*, float*, int64_t, cudaStream_t);
+template int launch_simt_forward<double, double>(const sos_plan_s*, const double*, double*, int64_t, cudaStream_t);
+template int launch_simt_forward<float, double>(const sos_plan_s*, const float*, double*, int64_t, cudaStream_t);
+template int launch_residual<float>(const sos_plan_s*, const float*, const float*, float*, double*, double*,
+                                    int32_t*, int64_t, cudaStream_t);
+template int launch_residual<double>(const sos_plan_s*, const double*, const double*, double*, double*,
+                                     double*, int32_t*, int64_t, cudaStream_t);
+template int launch_simt_adjoint<float>(const sos_plan_s*, const float*, const float*, float*, int64_t,
+                                        cudaStream_t);
+template int launch_simt_adjoint<double>(const sos_plan_s*, const double*, const double*, double*, int64_t,
+                                         cudaStream_t);
+template int launch_update<float>(int64_t, int64_t, float*, float*, float*, const float*, int, int64_t, double,
+                                  double, double, double, void*, int64_t, cudaStream_t);
+template int launch_update<double>(int64_t, int64_t, double*, double*, double*, const double*, int, int64_t,
+                                   double, double, double, double, void*, int64_t, cudaStream_t);
+template int launch_fill<float>(float*, int64_t, float, cudaStream_t);
+template int launch_fill<double>(double*, int64_t, double, cudaStream_t);
+
+}  // namespace sos

@@ -1,0 +1,153 @@
+"""Python front end of the C ABI.  torch provides device memory and streams;
+every computation is a call into ``libsos_gb300.so``.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DTYPE = {L.SOS_BF16: torch.float32, L.SOS_FP32: torch.float32, L.SOS_FP64: torch.float64}
+
+
+def _prec(prec) -> int:
+    return L.PREC[prec] if isinstance(prec, str) else int(prec)
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Plan:
+    """Monomial tables and device state for degree <= two_d in n variables with
+    r squares (default r = N, the paper's full-rank over-parameterisation)."""
+
+    def __init__(self, n: int, two_d: int, r: int | None = None):
+        from math import comb
+        N = comb(n + two_d // 2, two_d // 2)
+        self.n, self.two_d = n, two_d
+        self.handle = L.sos_plan_create(n, two_d, int(r if r is not None else N))
+        self.N, self.M, self.r = L.sos_plan_sizes(self.handle)
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                L.sos_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    # -- host tables ----------------------------------------------------------
+    def monomials(self, which: int = 0) -> np.ndarray:
+        rows = self.N if which == 0 else self.M
+        out = np.zeros((rows, self.n), dtype=np.uint8)
+        L.sos_plan_monomials(self.handle, which, out.ctypes.data)
+        return out
+
+    def idx(self) -> np.ndarray:
+        out = np.zeros((self.N, self.N), dtype=np.int32)
+        L.sos_plan_idx(self.handle, out.ctypes.data)
+        return out
+
+    # -- workspace ------------------------------------------------------------
+    def workspace(self, prec, device=None) -> torch.Tensor:
+        prec = _prec(prec)
+        device = torch.device(device or "cuda")
+        key = prec
+        ws = self._ws.get(key)
+        if ws is None:
+            nbytes = L.sos_workspace_size(self.handle, prec)
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            L.sos_workspace_init(self.handle, prec, _ptr(ws), _stream_handle())
+            self._ws[key] = ws
+        return ws
+
+    def _check(self, A: torch.Tensor, prec: int):
+        if not A.is_cuda or A.dtype != _DTYPE[prec] or not A.is_contiguous():
+            raise ValueError(f"A must be a contiguous CUDA {_DTYPE[prec]} tensor")
+        if tuple(A.shape[-2:]) != (self.N, self.r):
+            raise ValueError(f"A must be {self.N} x {self.r}, got {tuple(A.shape)}")
+
+    # -- one pass ---------------------------------------------------------------
+    def coeffs(self, A: torch.Tensor, prec="fp32") -> torch.Tensor:
+        prec = _prec(prec)
+        self._check(A, prec)
+        c = torch.empty(self.M, dtype=torch.float64 if prec == L.SOS_FP64 else torch.float32,
+                        device=A.device)
+        L.sos_coeffs(self.handle, prec, _ptr(A), _ptr(c), _ptr(self.workspace(prec, A.device)),
+                     _stream_handle())
+        return c
+
+    def loss_grad(self, A: torch.Tensor, p: torch.Tensor, prec="fp32", want_grad=True):
+        """(loss, ||p||^2, grad) with loss = 1/2 ||c(A) - p||^2; device tensors."""
+        prec = _prec(prec)
+        self._check(A, prec)
+        out = torch.empty(2, dtype=torch.float64, device=A.device)
+        grad = torch.empty_like(A) if want_grad else None
+        L.sos_loss_grad(self.handle, prec, _ptr(A), _ptr(p), _ptr(grad), _ptr(out),
+                        _ptr(self.workspace(prec, A.device)), _stream_handle())
+        return out[0], out[1], grad
+
+    def loss_grad_batched(self, A: torch.Tensor, p: torch.Tensor, prec="fp32", want_grad=True):
+        prec = _prec(prec)
+        batch = A.shape[0]
+        self._check(A, prec)
+        nbytes = L.sos_workspace_size_batched(self.handle, prec, batch)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=A.device)
+        L.sos_workspace_init(self.handle, prec, _ptr(ws), _stream_handle())
+        out = torch.empty(batch, 2, dtype=torch.float64, device=A.device)
+        grad = torch.empty_like(A) if want_grad else None
+        L.sos_loss_grad_batched(self.handle, prec, batch, _ptr(A), _ptr(p), _ptr(grad), _ptr(out),
+                                _ptr(ws), _stream_handle())
+        return out[:, 0], out[:, 1], grad
+
+    def status(self, prec) -> int:
+        prec = _prec(prec)
+        ws = self._ws.get(prec)
+        if ws is None:
+            return L.SOS_OK
+        return L.sos_read_status(self.handle, prec, _ptr(ws), _stream_handle())
+
+    def certify(self, A: torch.Tensor, p64: torch.Tensor, tol: float = 1e-8):
+        """(relative FP64 residual, verdict)."""
+        if A.dtype not in (torch.float32, torch.float64):
+            raise ValueError("A must be float32 or float64")
+        return L.sos_certify(self.handle, _ptr(A), A.dtype == torch.float64, _ptr(p64), tol,
+                             _stream_handle())
+
+
+class Optimizer:
+    """Adam (the paper's optimiser, Sec. 3) or GD state for one A, stepping
+    through sos_step."""
+
+    def __init__(self, plan: Plan, A: torch.Tensor, prec="bf16", optimizer="adam", lr=1e-2,
+                 beta1=0.9, beta2=0.999, eps=1e-8):
+        self.plan, self.prec = plan, _prec(prec)
+        plan._check(A, self.prec)
+        self.A = A
+        self.opts = L.sos_step_opts(L.SOS_ADAM if optimizer == "adam" else L.SOS_GD, lr, beta1,
+                                    beta2, eps)
+        if optimizer == "adam":
+            self.m, self.v = torch.zeros_like(A), torch.zeros_like(A)
+        else:
+            self.m = self.v = None
+        self.state = L.sos_state(_ptr(A), _ptr(self.m), _ptr(self.v), 0)
+        self.loss = torch.zeros(2, dtype=torch.float64, device=A.device)
+
+    @property
+    def t(self) -> int:
+        return self.state.t
+
+    def step(self, p: torch.Tensor) -> torch.Tensor:
+        """One iteration; returns the device tensor {loss before the step, ||p||^2}."""
+        L.sos_step(self.plan.handle, self.prec, self.state, _ptr(p), self.opts, _ptr(self.loss),
+                   _ptr(self.plan.workspace(self.prec, self.A.device)), _stream_handle())
+        return self.loss

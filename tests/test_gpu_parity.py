@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle
+on the same seeded inputs.
+
+Tolerances (written here, derived from the arithmetic):
+  * FP64 path: 1e-12 relative (normwise) -- only summation order differs.
+  * FP32 path (CUDA cores, no TF32): loss and gradient within 1e-5 relative,
+    normwise, at a random A -- the accuracy the method is asked to hold.
+  * BF16 path: the contractions see A rounded to bf16 and, in the adjoint,
+    the residual rounded to bf16 (unit roundoff 2^-8: bf16 keeps 8 bits of
+    significand).  The forward is compared with the oracle at the
+    bf16-rounded A (1e-5 normwise: FP32 accumulation only); the gradient
+    with the oracle at the same A, inside the elementwise bound
+    (2^-8 + 4 N 2^-24) * 2 |H(r)| |A| that the rounding of r and the FP32
+    accumulation over N terms imply.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import sos_inputs
+from paper_2410_19844_gb300 import _lib as L
+from paper_2410_19844_gb300.engine import Optimizer, Plan
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    return torch.from_numpy(x).float().bfloat16().double().numpy()
+
+
+def problem(n, two_d, r=None, seed=0, squares=5):
+    o = oracle.Oracle(n, two_d)
+    r = o.N if r is None else r
+    A = sos_inputs.normal_matrix(o.N, r, seed=seed, sigma=0.3)
+    G = sos_inputs.normal_matrix(o.N, squares, seed=seed + 1)
+    p = o.coeffs(G)
+    return o, A, p
+
+
+# -- the tcgen05 GEMM core ------------------------------------------------------------
+
+@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 512, 128), (200, 300, 100), (384, 256, 1000)])
+@pytest.mark.parametrize("b_mn", [0, 1])
+def test_tc_gemm_matches_fp64_matmul(m, n, k, b_mn):
+    g = torch.Generator().manual_seed(m * 7 + n * 3 + k + b_mn)
+    X = torch.randn(m, k, generator=g).bfloat16()
+    Y = torch.randn(k, n, generator=g).bfloat16() if b_mn else torch.randn(n, k, generator=g).bfloat16()
+    ref = X.double() @ (Y.double() if b_mn else Y.double().T)
+    ldx = (k + 63) // 64 * 64
+    ldy = ((n if b_mn else k) + 63) // 64 * 64
+    Xd = torch.zeros(m, ldx, dtype=torch.bfloat16, device=DEV)
+    Xd[:, :k] = X.to(DEV)
+    Yd = torch.zeros(Y.shape[0], ldy, dtype=torch.bfloat16, device=DEV)
+    Yd[:, :Y.shape[1]] = Y.to(DEV)
+    D = torch.full((m, n), float("nan"), dtype=torch.float32, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    L.sos_diag_gemm_bf16(b_mn, Xd.data_ptr(), Yd.data_ptr(), D.data_ptr(), m, n, k, ldx, ldy,
+                         status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert int(status.item()) == 0
+    got = D.double().cpu().numpy()
+    # FP32 accumulation of exact bf16 products: 4 k 2^-24 sum|x||y| (a layout
+    # mistake gives errors of the size of the entries themselves)
+    bound = 4 * k * 2.0 ** -24 * (X.double().abs() @ (Y.double().abs() if b_mn else Y.double().abs().T)).numpy()
+    assert np.all(np.abs(got - ref.numpy()) <= bound + 1e-30)
+
+
+# -- forward --------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,two_d,r", [(3, 4, 10), (4, 6, 9), (6, 8, 210), (5, 6, 300), (2, 10, 21)])
+def test_forward_fp64(n, two_d, r):
+    o, A, _ = problem(n, two_d, r)
+    pl = Plan(n, two_d, r)
+    c = pl.coeffs(torch.from_numpy(A).to(DEV), "fp64").cpu().numpy()
+    assert rel(c, o.coeffs(A)) < 1e-12
+
+
+@pytest.mark.parametrize("n,two_d,r", [(6, 8, 210), (5, 6, 300), (7, 6, 50), (8, 4, 45)])
+def test_forward_fp32(n, two_d, r):
+    o, A, _ = problem(n, two_d, r)
+    pl = Plan(n, two_d, r)
+    c = pl.coeffs(torch.from_numpy(A).float().to(DEV), "fp32").cpu().numpy()
+    assert rel(c, o.coeffs(A.astype(np.float32).astype(np.float64))) < 1e-5
+
+
+@pytest.mark.parametrize("n,two_d,r", [(6, 8, 210), (5, 6, 300), (7, 8, 130), (9, 6, 700), (3, 4, 10)])
+def test_forward_bf16(n, two_d, r):
+    o, A, _ = problem(n, two_d, r)
+    pl = Plan(n, two_d, r)
+    c = pl.coeffs(torch.from_numpy(A).float().to(DEV), "bf16").cpu().numpy()
+    assert rel(c, o.coeffs(bf16_round(A))) < 1e-5
+
+
+# -- loss and gradient ---------------------------------------------------------------
+
+@pytest.mark.parametrize("n,two_d,r", [(3, 4, 10), (4, 6, 35), (6, 8, 210), (5, 6, 77)])
+def test_loss_grad_fp64(n, two_d, r):
+    o, A, p = problem(n, two_d, r)
+    pl = Plan(n, two_d, r)
+    loss, pp, g = pl.loss_grad(torch.from_numpy(A).to(DEV), torch.from_numpy(p).to(DEV), "fp64")
+    loss_ref, g_ref, _ = o.loss_grad(A, p)
+    assert abs(loss.item() - loss_ref) <= 1e-12 * loss_ref
+    assert abs(pp.item() - np.dot(p, p)) <= 1e-12 * np.dot(p, p)
+    assert rel(g.cpu().numpy(), g_ref) < 1e-12
+
+
+@pytest.mark.parametrize("n,two_d,r", [(6, 8, 210), (5, 6, 300), (7, 6, 50), (4, 10, 1001), (8, 4, 45)])
+def test_loss_grad_fp32(n, two_d, r):
+    o, A, p = problem(n, two_d, r)
+    A32 = A.astype(np.float32)
+    p32 = p.astype(np.float32)
+    pl = Plan(n, two_d, r)
+    loss, _, g = pl.loss_grad(torch.from_numpy(A32).to(DEV), torch.from_numpy(p32).to(DEV), "fp32")
+    loss_ref, g_ref, _ = o.loss_grad(A32.astype(np.float64), p32.astype(np.float64))
+    assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+    assert rel(g.cpu().numpy(), g_ref) < 1e-5
+
+
+@pytest.mark.parametrize("n,two_d,r", [(6, 8, 210), (5, 6, 300), (7, 8, 130), (9, 6, 700)])
+def test_loss_grad_bf16(n, two_d, r):
+    o, A, p = problem(n, two_d, r)
+    A16 = bf16_round(A)
+    p32 = p.astype(np.float32).astype(np.float64)
+    pl = Plan(n, two_d, r)
+    loss, _, g = pl.loss_grad(torch.from_numpy(A).float().to(DEV), torch.from_numpy(p32).float().to(DEV),
+                              "bf16")
+    c_ref = o.coeffs(A16)
+    loss_ref, resid = o.residual(c_ref, p32)
+    g_ref = o.grad_from_resid(A16, resid)
+    assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+    terms = o.grad_from_resid(np.abs(A16), np.abs(resid))      # 2 |H(r)| |A|
+    bound = (2.0 ** -8 + 4 * o.N * 2.0 ** -24) * terms + 1e-30
+    assert np.all(np.abs(g.cpu().numpy() - g_ref) <= bound)
+
+
+def test_loss_only_skips_gradient():
+    o, A, p = problem(4, 6)
+    pl = Plan(4, 6)
+    loss, _, g = pl.loss_grad(torch.from_numpy(A).to(DEV), torch.from_numpy(p).to(DEV), "fp64",
+                              want_grad=False)
+    assert g is None
+    assert abs(loss.item() - o.loss(A, p)) <= 1e-12 * o.loss(A, p)
+
+
+# -- batched FP32 (64 instances of n=6, 2d=8, 50 squares each) ------------------------------
+
+def test_batched_fp32_matches_oracle_and_differences():
+    w = sos_inputs.BATCH
+    o = oracle.Oracle(w.n, w.two_d)
+    pl = Plan(w.n, w.two_d)
+    batch = 64
+    As = np.stack([sos_inputs.init_A(w, s) for s in range(batch)]).astype(np.float32)
+    ps = np.stack([o.coeffs(sos_inputs.generator(w, s)) for s in range(batch)]).astype(np.float32)
+    loss, _, g = pl.loss_grad_batched(torch.from_numpy(As).to(DEV), torch.from_numpy(ps).to(DEV), "fp32")
+    loss, g = loss.cpu().numpy(), g.cpu().numpy()
+    rng = np.random.default_rng(5)
+    for s in [0, 1, 31, 63]:
+        A64, p64 = As[s].astype(np.float64), ps[s].astype(np.float64)
+        loss_ref, g_ref, _ = o.loss_grad(A64, p64)
+        assert abs(loss[s] - loss_ref) <= 1e-5 * loss_ref
+        assert rel(g[s], g_ref) < 1e-5
+        # central differences with h = 1e-3 in FP64, Richardson-combined (exact for a quartic)
+        for _ in range(32):
+            e = (int(rng.integers(o.N)), int(rng.integers(o.N)))
+            E = np.zeros_like(A64)
+            E[e] = 1.0
+
+            def D(h):
+                return (o.loss(A64 + h * E, p64) - o.loss(A64 - h * E, p64)) / (2 * h)
+            fd = (4 * D(0.5e-3) - D(1e-3)) / 3
+            assert abs(g[s][e] - fd) <= 1e-5 * np.abs(g_ref).max()
+
+
+# -- optimiser step -------------------------------------------------------------------
+
+@pytest.mark.parametrize("optimizer", ["adam", "gd"])
+def test_step_fp64_matches_oracle(optimizer):
+    o, A, p = problem(3, 4)
+    A_dev = torch.from_numpy(A.copy()).to(DEV)
+    pl = Plan(3, 4)
+    opt = Optimizer(pl, A_dev, prec="fp64", optimizer=optimizer, lr=1e-2)
+    p_dev = torch.from_numpy(p).to(DEV)
+    Aref, m, v = A.copy(), np.zeros_like(A), np.zeros_like(A)
+    for t in range(1, 6):
+        loss = opt.step(p_dev)[0].item()
+        loss_ref, g, _ = o.loss_grad(Aref, p)
+        assert abs(loss - loss_ref) <= 1e-12 * loss_ref
+        if optimizer == "adam":
+            o.adam_step(Aref, m, v, g, t, lr=1e-2)
+        else:
+            o.gd_step(Aref, g, 1e-2)
+        assert rel(A_dev.cpu().numpy(), Aref) < 1e-12
+
+
+# -- certificate and status ---------------------------------------------------------------
+
+def test_certify_generating_matrix():
+    o = oracle.Oracle(4, 6)
+    A0 = sos_inputs.normal_matrix(o.N, o.N, seed=3)
+    p = o.coeffs(A0)
+    pl = Plan(4, 6)
+    rel_res, verdict = pl.certify(torch.from_numpy(A0).to(DEV), torch.from_numpy(p).to(DEV))
+    assert rel_res <= 1e-14 and verdict == L.SOS_VERDICT_SOS
+    A1 = sos_inputs.normal_matrix(o.N, o.N, seed=4)
+    rel_res, verdict = pl.certify(torch.from_numpy(A1).float().to(DEV), torch.from_numpy(p).to(DEV))
+    want = o.certify(o.coeffs(A1.astype(np.float32).astype(np.float64)), p)
+    assert abs(rel_res - want) <= 1e-12 * want and verdict == L.SOS_VERDICT_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_nonfinite_target_sets_status(prec):
+    o, A, p = problem(4, 6)
+    p[3] = np.nan
+    pl = Plan(4, 6)
+    pl.loss_grad(torch.from_numpy(A).float().to(DEV), torch.from_numpy(p).float().to(DEV), prec)
+    assert pl.status(prec) == L.SOS_E_NONFINITE
+    assert pl.status(prec) == L.SOS_OK      # read-and-clear
