@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput of the loss-and-gradient step with its gradient-descent update.
+
+Workload (one step = forward c(A) = sum_k q_k^2, residual and loss, adjoint
+2 H(c - p) A, GD update): n = 20 variables, degree 2d = 8, N = r = 10,626
+monomials/squares, M = 3,108,105 coefficients; target p = sum of 2000 squares
+of N(0, 1)/sqrt(N) polynomials; A0 ~ N(0, 0.1^2); seeded, synthetic.  Every
+operand is larger than L2 (bf16 A 226 MB, bf16 H 226 MB, index table 451 MB),
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank runs its own independent problem
+(replicas; the step has no cross-GPU exchange in this build) and `value` is
+the sum over ranks.  `--impl reference` times the CPU oracle on the same
+workload (a bounded column sample, extrapolated) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GD iters/s at ~3.1M coeffs"
+UNIT = "iters/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="large_n20_2d8")
+    ap.add_argument("--lr", type=float, default=1e-7)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0,
+                "source": "fallback"}
+
+
+# -- clocks during the timed region ------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                    rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+                except (ValueError, IndexError):
+                    continue
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        use = inside or rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples_in_region": len(inside), "samples": len(use)}
+
+
+# -- traffic figures committed from ncu -------------------------------------------------
+
+def committed_traffic(kernel: str):
+    """dram bytes per launch from profiles/traffic.json, or None when the kernel
+    source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        rec = d[kernel]
+        src = os.path.join(ROOT, rec["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return rec["bytes_per_launch"] if sha == rec["source_sha"] else None
+    except Exception:
+        return None
+
+
+# -- CPU oracle sample --------------------------------------------------------------
+
+def oracle_sample(w, widths=(8, 16), reps=2, seed=0):
+    """Times one oracle GD iteration (coefficients, residual, gradient, update) on
+    column slices of A and extrapolates linearly in the number of columns: the
+    oracle's cost is a + b * columns (pair-table lookups plus per-column dot
+    products and axpys).  Returns (iters/s for the full workload, description)."""
+    import numpy as np
+
+    import oracle
+    import sos_inputs
+    t_setup = time.time()
+    o = oracle.Oracle(w.n, w.two_d)
+    _ = o.prod
+    p = sos_inputs.normal_matrix(w.M, 1, seed)[:, 0]     # values do not change the cost
+    setup_s = time.time() - t_setup
+    times = {}
+    for cols in widths:
+        A = sos_inputs.normal_matrix(w.N, cols, seed, sigma=w.init_sigma)
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            loss, grad, _c = o.loss_grad(A, p)
+            o.gd_step(A, grad, 1e-7)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        times[cols] = best
+    (c1, t1), (c2, t2) = sorted(times.items())
+    t2 = max(t2, t1)
+    b = (t2 - t1) / (c2 - c1)
+    a = max(t1 - b * c1, 0.0)
+    t_full = a + b * w.cols
+    desc = (f"oracle GD iteration on column slices of width {list(times)} of the {w.N} x {w.cols} A "
+            f"(full M = {w.M}), best of {reps}: {', '.join(f'{k} cols {v:.3f} s' for k, v in times.items())}; "
+            f"fit t = {a:.3f} s + {b:.4f} s/col, extrapolated to {w.cols} cols = {t_full:.1f} s/iter; "
+            f"setup (tables) {setup_s:.1f} s not timed")
+    return 1.0 / t_full, desc, oracle.num_threads()
+
+
+def run_reference(args):
+    import sos_inputs
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    w = sos_inputs.WORKLOADS[args.workload]
+    o = oracle.Oracle(w.n, w.two_d)
+    t0 = time.time()
+    _ = o.prod
+    p = sos_inputs.normal_matrix(w.M, 1, 0)[:, 0]          # values do not change the cost
+    setup = time.time() - t0
+    cols = 8
+    A = sos_inputs.normal_matrix(w.N, cols, 0, sigma=w.init_sigma)
+
+    def step():
+        loss, grad, _c = o.loss_grad(A, p)
+        o.gd_step(A, grad, 1e-7)
+
+    # a second width, once, gives the column-independent part of the cost
+    A2 = sos_inputs.normal_matrix(w.N, 2 * cols, 1, sigma=w.init_sigma)
+    for _ in range(args.warmup):
+        step()
+    t_2 = None
+    for _ in range(2):
+        t_a = time.perf_counter()
+        o.loss_grad(A2, p)
+        dt = time.perf_counter() - t_a
+        t_2 = dt if t_2 is None else min(t_2, dt)
+    t_a = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    t_1 = (time.perf_counter() - t_a) / args.steps
+    b = max((t_2 - t_1) / cols, t_1 / cols * 0.5)
+    a = max(t_1 - b * cols, 0.0)
+    t_full = a + b * w.cols
+    value = 1.0 / t_full
+    sample = (f"each step: one oracle GD iteration on a {w.N} x {cols} column slice of A (full M = {w.M}); "
+              f"{t_1:.3f} s/step, {2 * cols} columns {t_2:.3f} s; cost a + b*cols with a = {a:.3f} s, "
+              f"b = {b:.4f} s/col, extrapolated to {w.cols} columns = {t_full:.1f} s/iter; "
+              f"table setup {setup:.1f} s untimed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_full,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(w, world):
+    return {"workload": w.name, "n": w.n, "two_d": w.two_d, "N": w.N, "M": w.M, "r": w.cols,
+            "target_squares": w.squares, "optimizer": "gd",
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs exceed L2 (bf16 A 226 MB, bf16 H 226 MB, idx 451 MB); no flush"}
+
+
+# -- our arm -------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import sos_inputs
+    from paper_2410_19844_gb300 import _lib as L
+    from paper_2410_19844_gb300.engine import Optimizer, Plan
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = sos_inputs.WORKLOADS[args.workload]
+    L.lib()
+
+    # inputs: target p = c(G) by the library's own FP64 forward; A0 ~ N(0, 0.1^2)
+    G = torch.from_numpy(sos_inputs.generator(w, rank)).to(dev)
+    p64 = Plan(w.n, w.two_d, r=G.shape[1]).coeffs(G.contiguous(), "fp64")
+    p = p64.float().contiguous()
+    del G
+    A0 = torch.from_numpy(sos_inputs.init_A(w, rank).astype(np.float32))
+    plan = Plan(w.n, w.two_d)
+    A = A0.to(dev).contiguous()
+    opt = Optimizer(plan, A, prec="bf16", optimizer="gd", lr=args.lr)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        opt.step(p)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    L.sos_timing_reset()
+    L.sos_timing_enable(True)
+    launches0 = L.sos_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        opt.step(p)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if world > 1:
+        dist.barrier()
+    launches = L.sos_launch_count() - launches0
+    L.sos_timing_enable(False)
+    kernels = L.sos_timing_report()
+    L.sos_timing_reset()
+    clocks = sampler.stop(t_wall0, t_wall1)
+    elapsed_ms = e0.elapsed_time(e1)
+    status = plan.status("bf16")
+    loss_now = float(opt.loss[0].item())
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms / 1000.0)
+
+    # roofline of the dominant kernel, from the events recorded in the timed region
+    N, r = w.N, w.cols
+    alg_flops = {"tc_forward": float(N) * N * r, "tc_adjoint": 2.0 * N * N * r}
+    peaks = measured_peaks()
+    dom = max(kernels.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    avg_ms = dom_ms / dom_launches
+    roof = None
+    if dom_name in alg_flops:
+        achieved = alg_flops[dom_name] / (avg_ms / 1000.0) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "peak_kind": f"bf16 sustained, {peaks['source']}",
+                "frac_of_burst": achieved / peaks["bf16_tflops"],
+                "alg_flops_per_launch": alg_flops[dom_name], "avg_launch_ms": avg_ms,
+                "traffic": committed_traffic(dom_name)}
+    step_tflops = (alg_flops["tc_forward"] + alg_flops["tc_adjoint"]) / (ms_per_step / 1000.0) / 1e12
+    per_kernel = {k: {"launches": n, "ms_per_launch": ms / n} for k, (n, ms) in kernels.items()}
+
+    # end to end through the public API, state in pinned host memory every step
+    e2e = None
+    if not args.no_e2e:
+        A_host = A0.clone().pin_memory()
+        p_host = p.cpu().pin_memory()
+        loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
+        A_dev = torch.empty_like(A)
+        p_dev = torch.empty_like(p)
+        opt2 = Optimizer(plan, A_dev, prec="bf16", optimizer="gd", lr=args.lr)
+        k2 = max(1, min(args.e2e_steps, args.steps))
+
+        def e2e_step():
+            A_dev.copy_(A_host, non_blocking=True)
+            p_dev.copy_(p_host, non_blocking=True)
+            opt2.step(p_dev)
+            loss_host.copy_(opt2.loss, non_blocking=True)
+            A_host.copy_(A_dev, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(2):
+            e2e_step()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        abytes = A.numel() * 4
+        e2e = {"value": world * k2 / (e2e_ms / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": abytes + p.numel() * 4, "d2h_bytes_per_step": abytes + 16,
+               "steps": k2, "ms_per_step": e2e_ms / k2,
+               "note": "state (A, p) copied host->device and A, loss device->host every step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, cores = oracle_sample(w)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": config_of(w, world), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu,
+                "step": {"alg_tflops": step_tflops,
+                         "frac_of_sustained": step_tflops / peaks["bf16_tflops_sustained"],
+                         "frac_of_burst": step_tflops / peaks["bf16_tflops"],
+                         "kernels": per_kernel, "status": status, "loss_after": loss_now}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

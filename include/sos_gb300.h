@@ -176,6 +176,22 @@ int sos_diag_gemm_bf16(int b_mn_major, const void* X, const void* Y, float* D,
                        int64_t m, int64_t n, int64_t k, int64_t ldx, int64_t ldy,
                        int32_t* status, void* stream);
 
+/* ---- instrumentation ------------------------------------------------------ */
+
+/* Number of kernels this library has launched since it was loaded. */
+int64_t sos_launch_count(void);
+
+/* on != 0: bracket every kernel launch with CUDA events on its stream
+ * (device-side timing, stream-ordered; do not enable during graph capture). */
+int sos_timing_enable(int on);
+
+/* Drops the recorded events (waits for them first). */
+int sos_timing_reset(void);
+
+/* Writes one line per kernel, "name launches total_ms\n", for the launches
+ * recorded since the last reset.  Waits for the recorded events. */
+int sos_timing_report(char* buf, size_t cap);
+
 const char* sos_last_error(void);
 
 #ifdef __cplusplus

@@ -27,7 +27,8 @@ EXPORTS = [
     "sos_plan_create", "sos_plan_destroy", "sos_plan_sizes", "sos_plan_monomials", "sos_plan_idx",
     "sos_workspace_size", "sos_workspace_init", "sos_coeffs", "sos_loss_grad",
     "sos_workspace_size_batched", "sos_loss_grad_batched", "sos_step", "sos_read_status",
-    "sos_certify", "sos_diag_gemm_bf16", "sos_last_error",
+    "sos_certify", "sos_diag_gemm_bf16", "sos_launch_count", "sos_timing_enable",
+    "sos_timing_reset", "sos_timing_report", "sos_last_error",
 ]
 
 
@@ -86,6 +87,14 @@ def lib(auto_build: bool = True):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = i32
+    L.sos_launch_count.argtypes = []
+    L.sos_launch_count.restype = i64
+    L.sos_timing_enable.argtypes = [i32]
+    L.sos_timing_enable.restype = i32
+    L.sos_timing_reset.argtypes = []
+    L.sos_timing_reset.restype = i32
+    L.sos_timing_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    L.sos_timing_report.restype = i32
     L.sos_last_error.argtypes = []
     L.sos_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -174,3 +183,26 @@ def sos_diag_gemm_bf16(b_mn_major, X, Y, D, m, n, k, ldx, ldy, status, stream) -
 
 def sos_last_error() -> str:
     return lib().sos_last_error().decode(errors="replace")
+
+
+def sos_launch_count() -> int:
+    return int(lib().sos_launch_count())
+
+
+def sos_timing_enable(on: bool) -> None:
+    _check(lib().sos_timing_enable(1 if on else 0))
+
+
+def sos_timing_reset() -> None:
+    _check(lib().sos_timing_reset())
+
+
+def sos_timing_report() -> dict:
+    """{kernel name: (launches, total ms)} since the last reset."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().sos_timing_report(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, count, ms = line.split()
+        out[name] = (int(count), float(ms))
+    return out

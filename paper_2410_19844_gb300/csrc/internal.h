@@ -29,6 +29,22 @@ int cuda_fail(cudaError_t e, const char* what);
         if (s_ != SOS_OK) return s_;    \
     } while (0)
 
+// Counts every kernel launch and, when timing is on, brackets it with CUDA
+// events on the launching stream (see timing.cpp).  Construct it right
+// before the launch; it records the closing event when it goes out of scope.
+class KernelScope {
+   public:
+    KernelScope(const char* name, cudaStream_t st);
+    ~KernelScope();
+    KernelScope(const KernelScope&) = delete;
+    KernelScope& operator=(const KernelScope&) = delete;
+
+   private:
+    const char* name_;
+    cudaStream_t st_;
+    cudaEvent_t start_ = nullptr;
+};
+
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
 

@@ -346,13 +346,19 @@ int launch_build_idx(const sos_plan_s* p, int32_t* idx, const uint8_t* d_S, cons
     if (smem > 48 * 1024) return fail(SOS_E_UNSUPPORTED, "build_idx: n * (2d+1) too large");
     dim3 grid((unsigned)std::min<int64_t>(ceil_div(p->ld_idx, kThreads), 64),
               (unsigned)std::min<int64_t>(p->N, 65535));
-    build_idx_kernel<<<grid, kThreads, smem, st>>>(p->n, W, p->N, p->ld_idx, d_S, d_phi, idx);
+    {
+        KernelScope ks_("build_idx", st);
+        build_idx_kernel<<<grid, kThreads, smem, st>>>(p->n, W, p->N, p->ld_idx, d_S, d_phi, idx);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
 
 int launch_cast_bf16(const float* A, int64_t N, int64_t r, void* a16, int64_t ld16, cudaStream_t st) {
-    cast_bf16_kernel<<<grid_for(N * r), kThreads, 0, st>>>(A, N, r, (__nv_bfloat16*)a16, ld16);
+    {
+        KernelScope ks_("cast_bf16", st);
+        cast_bf16_kernel<<<grid_for(N * r), kThreads, 0, st>>>(A, N, r, (__nv_bfloat16*)a16, ld16);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
@@ -362,8 +368,11 @@ int launch_simt_forward(const sos_plan_s* p, const Tin* A, Tacc* c, int64_t batc
     const int64_t T = ceil_div(p->N, 64);
     if (T > 65535 || batch > 65535) return fail(SOS_E_UNSUPPORTED, "simt_forward: too many tiles");
     dim3 grid((unsigned)T, (unsigned)T, (unsigned)batch);
-    simt_forward_kernel<Tin, Tacc><<<grid, kThreads, 0, st>>>(A, p->N, p->r, p->dev.idx, p->ld_idx, c,
-                                                              p->N * p->r, p->M);
+    {
+        KernelScope ks_("simt_forward", st);
+        simt_forward_kernel<Tin, Tacc><<<grid, kThreads, 0, st>>>(A, p->N, p->r, p->dev.idx, p->ld_idx, c,
+                                                                  p->N * p->r, p->M);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
@@ -375,7 +384,10 @@ int launch_residual(const sos_plan_s* p, const T* c, const T* pv, T* resid, doub
     int blocks = 1;
     if (batch == 1) blocks = (int)std::min<int64_t>(kResidBlocks, std::max<int64_t>(1, ceil_div(p->M, 4 * kThreads)));
     dim3 grid(blocks, (unsigned)batch);
-    residual_kernel<T><<<grid, kThreads, 0, st>>>(c, pv, resid, p->M, loss, partials, status, status + 1);
+    {
+        KernelScope ks_("residual", st);
+        residual_kernel<T><<<grid, kThreads, 0, st>>>(c, pv, resid, p->M, loss, partials, status, status + 1);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
@@ -386,16 +398,22 @@ int launch_simt_adjoint(const sos_plan_s* p, const T* A, const T* resid, T* grad
     const int64_t TI = ceil_div(p->N, 64), TK = ceil_div(p->r, 64);
     if (TI > 65535 || batch > 65535 || TK > INT32_MAX) return fail(SOS_E_UNSUPPORTED, "simt_adjoint: too many tiles");
     dim3 grid((unsigned)TK, (unsigned)TI, (unsigned)batch);
-    simt_adjoint_kernel<T><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r, grad,
-                                                      p->N * p->r, p->M);
+    {
+        KernelScope ks_("simt_adjoint", st);
+        simt_adjoint_kernel<T><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r, grad,
+                                                          p->N * p->r, p->M);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
 
 int launch_build_h16(const sos_plan_s* p, const float* resid, void* h16, cudaStream_t st) {
     const int64_t work = p->N * ceil_div(p->N, 8);
-    build_h16_kernel<<<grid_for(work, p->dev.num_sms * 8), kThreads, 0, st>>>(
-        resid, p->dev.idx, p->ld_idx, p->N, (__nv_bfloat16*)h16, p->ld16h);
+    {
+        KernelScope ks_("build_h16", st);
+        build_h16_kernel<<<grid_for(work, p->dev.num_sms * 8), kThreads, 0, st>>>(
+            resid, p->dev.idx, p->ld_idx, p->N, (__nv_bfloat16*)h16, p->ld16h);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
@@ -405,16 +423,22 @@ int launch_update(int64_t N, int64_t r, T* A, T* m, T* v, const T* grad, int opt
                   double lr, double b1, double b2, double eps, void* a16, int64_t ld16, cudaStream_t st) {
     const double c1 = 1.0 - std::pow(b1, (double)t);
     const double c2 = 1.0 - std::pow(b2, (double)t);
-    update_kernel<T><<<grid_for(N * r), kThreads, 0, st>>>(N, r, A, m, v, grad, optimizer, (T)lr, (T)b1,
-                                                           (T)b2, (T)eps, (T)c1, (T)c2,
-                                                           (__nv_bfloat16*)a16, ld16);
+    {
+        KernelScope ks_("update", st);
+        update_kernel<T><<<grid_for(N * r), kThreads, 0, st>>>(N, r, A, m, v, grad, optimizer, (T)lr, (T)b1,
+                                                               (T)b2, (T)eps, (T)c1, (T)c2,
+                                                               (__nv_bfloat16*)a16, ld16);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
 
 template <typename T>
 int launch_fill(T* x, int64_t count, T value, cudaStream_t st) {
-    fill_kernel<T><<<grid_for(count), kThreads, 0, st>>>(x, count, value);
+    {
+        KernelScope ks_("fill", st);
+        fill_kernel<T><<<grid_for(count), kThreads, 0, st>>>(x, count, value);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }

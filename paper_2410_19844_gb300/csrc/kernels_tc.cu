@@ -38,6 +38,7 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait, then give u
 
 // Forward: c[idx(a, b)] += w G_ab for b >= a.
 struct SegmentSumEpilogue {
+    static constexpr const char* kName = "tc_forward";
     int N;
     const int32_t* idx;
     int64_t ld_idx;
@@ -72,6 +73,7 @@ struct SegmentSumEpilogue {
 
 // Adjoint / diagnostic GEMM: out[row][col] = scale * acc.
 struct StoreEpilogue {
+    static constexpr const char* kName = "tc_adjoint";
     int rows, cols;
     int64_t ld;
     float scale;
@@ -86,6 +88,10 @@ struct StoreEpilogue {
         for (int j = 0; j < 32; ++j)
             if (k0 + j < cols) orow[j] = scale * __uint_as_float(v[j]);
     }
+};
+
+struct DiagEpilogue : StoreEpilogue {
+    static constexpr const char* kName = "tc_gemm_diag";
 };
 
 // ---- the GEMM core ---------------------------------------------------------------
@@ -297,7 +303,10 @@ static int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, co
     }
     if (num_tiles <= 0) return SOS_OK;
     const int grid = num_tiles < num_sms ? num_tiles : num_sms;
-    kern<<<grid, THREADS, SMEM_BYTES, st>>>(mA, mB, nkb, tiles, num_tiles, epi, status);
+    {
+        KernelScope ks_(Epi::kName, st);
+        kern<<<grid, THREADS, SMEM_BYTES, st>>>(mA, mB, nkb, tiles, num_tiles, epi, status);
+    }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
@@ -356,7 +365,12 @@ extern "C" int sos_diag_gemm_bf16(int b_mn_major, const void* X, const void* Y, 
     int rc = SOS_OK;
     cudaError_t e = cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "sos_diag_gemm_bf16: copy tiles");
-    StoreEpilogue epi{(int)m, (int)n, n, 1.0f, D};
+    DiagEpilogue epi;
+    epi.rows = (int)m;
+    epi.cols = (int)n;
+    epi.ld = n;
+    epi.scale = 1.0f;
+    epi.out = D;
     if (rc == SOS_OK) {
         rc = b_mn_major ? launch_gemm<true>(mA, mB, (int)ceil_div(k, BK), d_tiles, (int)tiles.size(), sms, epi,
                                             status, st)

@@ -16,6 +16,8 @@ Workload recipes (all float64, numpy ``default_rng(seed)``):
 * precision problem: n=10, 2d=10, r=N=3003; generator 1000 columns of N(0, 1).
 * large problem: n=20, 2d=8, r=N=10626; generator 2000 columns of
   N(0, 1)/sqrt(N); A0 ~ N(0, 0.1^2).
+* medium problem (profiling stand-in for the large one): n=18, 2d=8,
+  r=N=7315, same recipe.
 * serving stream: Poisson arrivals, n uniform in {3..8}, 2d uniform in
   {4, 6, 8}, r=N; even ids are sums of floor(N/2) random squares, odd ids are
   the same minus (p(x0) + 1) at x0 ~ N(0, I_n).
@@ -67,7 +69,9 @@ TINY = Workload("tiny_fp64_n3_2d4", 3, 4, 0, 5, "unit")
 BATCH = Workload("batch_fp32_n6_2d8", 6, 8, 0, 50, "unit")
 PRECISION = Workload("precision_n10_2d10", 10, 10, 0, 1000, "unit")
 LARGE = Workload("large_n20_2d8", 20, 8, 0, 2000, "inv_sqrt_n")
-WORKLOADS = {w.name: w for w in (TINY, BATCH, PRECISION, LARGE)}
+# a smaller case of the same kernels whose operands still exceed L2 (profiling)
+MEDIUM = Workload("medium_n18_2d8", 18, 8, 0, 2000, "inv_sqrt_n")
+WORKLOADS = {w.name: w for w in (TINY, BATCH, PRECISION, LARGE, MEDIUM)}
 
 
 def generator(w: Workload, seed: int) -> np.ndarray:

@@ -71,12 +71,13 @@ def _header_functions():
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names += re.findall(r"^\s*(?:int|const char\*)\s+(sos_\w+)\s*\(", text, flags=re.M)
+            names += re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(sos_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
 def test_library_exports_every_declared_symbol():
-    lib = ctypes.CDLL(L.lib().__dict__.get("_name", L.library_path()))
+    L.lib()
+    lib = ctypes.CDLL(L.library_path())
     names = _header_functions()
     assert len(names) >= 15
     for name in names:
