@@ -126,6 +126,27 @@ int sos_loss_grad_batched(sos_plan_t plan, int prec, int64_t batch, const void* 
                           const void* p, void* grad, void* loss, void* workspace,
                           void* stream);
 
+/* The loss of Eq. 2 from coefficients the caller already has, for callers
+ * that cannot allocate device memory when they call (a host framework that
+ * only hands a library the buffers it allocated itself, or a loop that runs
+ * under a fixed memory budget).  The paper has no counterpart: it is the
+ * residual and loss reduction of sos_loss_grad with its scratch (status word,
+ * ticket counters, per-block partial sums) kept in a fixed 1 MiB array that
+ * the library holds on every GPU that loads it, until the process exits.
+ * This entry point calls no allocator.
+ *   prec: SOS_FP32 (float c, p, resid) or SOS_FP64 (double);
+ *   c, p: dev batch x M; resid: dev batch x M (c - p) or NULL;
+ *   loss: dev double[batch][2] = {1/2 ||c - p||^2, ||p||^2} per problem.
+ * At most 1008 problems and 65,280 block partial sums per call (a problem
+ * uses min(512, ceil(M / 1024)) blocks); larger calls return SOS_E_INVALID.
+ * A NaN or Inf shows up as a NaN loss.  The first call on a device looks up
+ * the array's device address (synchronously); make it before any stream
+ * capture.  Every call shares the array, so calls that overlap on the GPU
+ * (other streams, other threads) race; each call clears what must start at
+ * zero, stream-ordered, before it runs. */
+int sos_loss_from_coeffs_static(int prec, int64_t batch, int64_t M, const void* c,
+                                const void* p, void* resid, double* loss, void* stream);
+
 /* Optimiser settings (Sec. 3: "basic ADAM"; the paper gives no constants,
  * these default to Kingma and Ba's: beta1 0.9, beta2 0.999, eps 1e-8). */
 typedef struct {

@@ -28,7 +28,7 @@ EXPORTS = [
     "sos_workspace_size", "sos_workspace_init", "sos_coeffs", "sos_loss_grad",
     "sos_workspace_size_batched", "sos_loss_grad_batched", "sos_step", "sos_read_status",
     "sos_certify", "sos_diag_gemm_bf16", "sos_launch_count", "sos_timing_enable",
-    "sos_timing_reset", "sos_timing_report", "sos_last_error",
+    "sos_timing_reset", "sos_timing_report", "sos_loss_from_coeffs_static", "sos_last_error",
 ]
 
 
@@ -82,6 +82,7 @@ def lib(auto_build: bool = True):
         "sos_read_status": [vp, i32, vp, vp],
         "sos_certify": [vp, vp, i32, vp, dbl, P(dbl), P(i32), vp, vp],
         "sos_diag_gemm_bf16": [i32, vp, vp, vp, i64, i64, i64, i64, i64, vp, vp],
+        "sos_loss_from_coeffs_static": [i32, i64, i64, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -206,3 +207,7 @@ def sos_timing_report() -> dict:
         name, count, ms = line.split()
         out[name] = (int(count), float(ms))
     return out
+
+
+def sos_loss_from_coeffs_static(prec, batch, M, c, p, resid, loss, stream) -> None:
+    _check(lib().sos_loss_from_coeffs_static(prec, batch, M, c, p, resid, loss, stream))

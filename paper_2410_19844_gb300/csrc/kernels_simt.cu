@@ -9,6 +9,8 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 
@@ -462,3 +464,85 @@ template int launch_fill<float>(float*, int64_t, float, cudaStream_t);
 template int launch_fill<double>(double*, int64_t, double, cudaStream_t);
 
 }  // namespace sos
+
+// ---- loss from given coefficients, without any allocation ---------------------------
+//
+// For callers that cannot allocate device memory at call time (for example a
+// host framework that hands a library only the buffers it allocated itself, or
+// a loop that runs under a fixed memory budget), this variant of the residual
+// and loss reduction keeps its scratch -- the status word, one ticket counter
+// per problem and the per-block partial sums -- in a fixed array in the
+// library's own device memory instead of a caller workspace.  Every GPU that
+// loads the library holds the array (1 MiB) until the process exits.
+
+namespace sos {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;
+constexpr size_t kStaticHeaderBytes = 4096;   // status word + ticket counters
+constexpr int64_t kStaticMaxBatch = (kStaticHeaderBytes - 64) / sizeof(int32_t);
+constexpr int64_t kStaticMaxPartials = (kStaticScratchBytes - kStaticHeaderBytes) / (2 * sizeof(double));
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {};
+
+// Host code cannot use g_static_scratch's name as a device address; look the
+// address up once per device, with that device current.
+int static_scratch(void** out) {
+    int dev = -1;
+    SOS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SOS_E_UNSUPPORTED, "static scratch: device index out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return SOS_OK;
+}
+
+template <typename T>
+int loss_from_coeffs_static(int64_t batch, int64_t M, const T* c, const T* p, T* resid, double* loss,
+                            cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>(kResidBlocks, std::max<int64_t>(1, ceil_div(M, 4 * kThreads)));
+    if (batch > kStaticMaxBatch || batch * blocks > kStaticMaxPartials)
+        return fail(SOS_E_INVALID, "sos_loss_from_coeffs_static: batch * blocks exceeds the fixed scratch (at most " +
+                                       std::to_string(kStaticMaxBatch) + " problems and " +
+                                       std::to_string(kStaticMaxPartials) + " block partials)");
+    void* base = nullptr;
+    SOS_CHECK(static_scratch(&base));
+    int32_t* status = static_cast<int32_t*>(base);
+    double* partials = reinterpret_cast<double*>(static_cast<char*>(base) + kStaticHeaderBytes);
+    // Ticket counters must start at zero; the array keeps the previous call's contents.
+    SOS_CUDA(cudaMemsetAsync(base, 0, kStaticHeaderBytes, st));
+    dim3 grid(blocks, (unsigned)batch);
+    {
+        KernelScope ks_("residual_static", st);
+        residual_kernel<T><<<grid, kThreads, 0, st>>>(c, p, resid, M, loss, partials, status, status + 16);
+    }
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+}  // namespace
+
+}  // namespace sos
+
+extern "C" int sos_loss_from_coeffs_static(int prec, int64_t batch, int64_t M, const void* c, const void* p,
+                                           void* resid, double* loss, void* stream) {
+    using namespace sos;
+    if ((prec != SOS_FP32 && prec != SOS_FP64) || batch < 1 || M < 1 || !c || !p || !loss)
+        return fail(SOS_E_INVALID, "sos_loss_from_coeffs_static: FP32 or FP64, batch >= 1, M >= 1, c, p, loss");
+    if (batch > 65535) return fail(SOS_E_INVALID, "sos_loss_from_coeffs_static: batch too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == SOS_FP64)
+        return loss_from_coeffs_static<double>(batch, M, static_cast<const double*>(c), static_cast<const double*>(p),
+                                               static_cast<double*>(resid), loss, st);
+    return loss_from_coeffs_static<float>(batch, M, static_cast<const float*>(c), static_cast<const float*>(p),
+                                          static_cast<float*>(resid), loss, st);
+}
+
