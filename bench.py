@@ -305,7 +305,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel, from the events recorded in the timed region
     N, r = w.N, w.cols
-    alg_flops = {"tc_forward": float(N) * N * r, "tc_adjoint": 2.0 * N * N * r}
+    alg_flops = {"tc_forward": float(N) * N * r, "tc_adjoint": 2.0 * N * N * r,
+                 "tc_adjoint_update": 2.0 * N * N * r}
     peaks = measured_peaks()
     dom = max(kernels.items(), key=lambda kv: kv[1][1])
     dom_name, (dom_launches, dom_ms) = dom
@@ -319,7 +320,7 @@ def run_ours(args):
                 "frac_of_burst": achieved / peaks["bf16_tflops"],
                 "alg_flops_per_launch": alg_flops[dom_name], "avg_launch_ms": avg_ms,
                 "traffic": committed_traffic(dom_name)}
-    step_tflops = (alg_flops["tc_forward"] + alg_flops["tc_adjoint"]) / (ms_per_step / 1000.0) / 1e12
+    step_tflops = 3.0 * N * N * r / (ms_per_step / 1000.0) / 1e12
     per_kernel = {k: {"launches": n, "ms_per_launch": ms / n} for k, (n, ms) in kernels.items()}
 
     # end to end through the public API, state in pinned host memory every step

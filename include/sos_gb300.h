@@ -157,16 +157,29 @@ typedef struct {
 
 /* Optimiser state, all dev, caller-owned: A (N x r) updated in place; m and
  * v (N x r, zero before the first Adam step; unused by GD); t = number of
- * steps already taken (incremented by sos_step). */
+ * steps already taken (incremented by sos_step).  flags belongs to the
+ * library: start it at 0, and set it back to 0 whenever A is changed outside
+ * sos_step or the state is stepped with another workspace.  With SOS_BF16 the
+ * workspace keeps a bf16 copy of A that sos_step refreshes from its fused
+ * update; flags records that the copy is current and which of two buffers
+ * holds it. */
 typedef struct {
     void* A;
     void* m;
     void* v;
     int64_t t;
+    int32_t flags;
+    int32_t reserved;
 } sos_state;
 
+#define SOS_STATE_BF16_CURRENT 1
+#define SOS_STATE_BF16_INDEX 2
+
 /* One iteration: loss and gradient at A, then the update of A (and m, v).
- * loss: dev double[2] = {loss before the update, ||p||^2}, or NULL. */
+ * loss: dev double[2] = {loss before the update, ||p||^2}, or NULL.
+ * SOS_BF16 fuses the update into the adjoint kernel's epilogue (the gradient
+ * is never stored); SOS_FP32 / SOS_FP64 store it in the workspace and update
+ * in a separate kernel. */
 int sos_step(sos_plan_t plan, int prec, sos_state* state, const void* p,
              const sos_step_opts* opts, void* loss, void* workspace, void* stream);
 

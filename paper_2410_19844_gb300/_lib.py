@@ -45,7 +45,7 @@ class sos_step_opts(ctypes.Structure):
 
 class sos_state(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_void_p), ("v", ctypes.c_void_p),
-                ("t", ctypes.c_int64)]
+                ("t", ctypes.c_int64), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None

@@ -169,9 +169,35 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
     SOS_CHECK(ensure_device(p));
     cudaStream_t st = (cudaStream_t)stream;
     const Workspace w = workspace_layout(p, prec);
+    const int64_t t = s->t + 1;
+    if (prec == SOS_BF16) {
+        // forward on the current bf16 copy, adjoint with the update fused into
+        // its epilogue, which writes the next bf16 copy
+        const size_t half = (size_t)p->N * (size_t)p->ld16 * 2;
+        const int cur = (s->flags & SOS_STATE_BF16_INDEX) ? 1 : 0;
+        char* a16_cur = at<char>(ws, w.a16) + cur * half;
+        char* a16_next = at<char>(ws, w.a16) + (1 - cur) * half;
+        int32_t* status = at<int32_t>(ws, w.status);
+        float* c = at<float>(ws, w.c);
+        float* resid = at<float>(ws, w.resid);
+        if (!(s->flags & SOS_STATE_BF16_CURRENT))
+            SOS_CHECK(launch_cast_bf16(static_cast<const float*>(s->A), p->N, p->r, a16_cur, p->ld16, st));
+        SOS_CUDA(cudaMemsetAsync(c, 0, (size_t)p->M * sizeof(float), st));
+        SOS_CHECK(launch_tc_forward(p, a16_cur, c, status, st));
+        double* L = loss ? static_cast<double*>(loss) : at<double>(ws, w.loss);
+        SOS_CHECK(launch_residual<float>(p, c, static_cast<const float*>(pv), resid, L, at<double>(ws, w.partials),
+                                         status, 1, st));
+        void* h16 = at<char>(ws, w.h16);
+        SOS_CHECK(launch_build_h16(p, resid, h16, st));
+        SOS_CHECK(launch_tc_adjoint_update(p, h16, a16_cur, a16_next, static_cast<float*>(s->A),
+                                           static_cast<float*>(s->m), static_cast<float*>(s->v), o->optimizer, t,
+                                           o->lr, o->beta1, o->beta2, o->eps, status, st));
+        s->flags = SOS_STATE_BF16_CURRENT | (cur ? 0 : SOS_STATE_BF16_INDEX);
+        s->t = t;
+        return SOS_OK;
+    }
     void* grad = at<char>(ws, w.grad);
     SOS_CHECK(loss_grad(p, prec, s->A, pv, grad, loss, ws, st));
-    const int64_t t = s->t + 1;
     if (prec == SOS_FP64)
         SOS_CHECK(launch_update<double>(p->N, p->r, static_cast<double*>(s->A), static_cast<double*>(s->m),
                                         static_cast<double*>(s->v), static_cast<const double*>(grad), o->optimizer,
@@ -180,6 +206,7 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         SOS_CHECK(launch_update<float>(p->N, p->r, static_cast<float*>(s->A), static_cast<float*>(s->m),
                                        static_cast<float*>(s->v), static_cast<const float*>(grad), o->optimizer, t,
                                        o->lr, o->beta1, o->beta2, o->eps, nullptr, 0, st));
+    s->flags = 0;
     s->t = t;
     return SOS_OK;
 }

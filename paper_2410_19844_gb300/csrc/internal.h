@@ -59,7 +59,7 @@ struct Workspace {
     size_t c = 0;          // M accumulators (float or double)
     size_t resid = 0;      // M residuals (float or double)
     size_t grad = 0;       // N x r gradient (float or double)
-    size_t a16 = 0;        // N x ld16 bf16 copy of A   (SOS_BF16 only)
+    size_t a16 = 0;        // 2 x N x ld16 bf16 copies of A, ping-pong (SOS_BF16 only)
     size_t h16 = 0;        // N x ld16h bf16 H(resid)   (SOS_BF16 only)
     size_t total = 0;
 };
@@ -125,5 +125,8 @@ int launch_tc_forward(const sos_plan_s* plan, const void* a16, float* c, int32_t
                       cudaStream_t st);
 int launch_tc_adjoint(const sos_plan_s* plan, const void* h16, const void* a16, float* grad,
                       int32_t* status, cudaStream_t st);
+int launch_tc_adjoint_update(const sos_plan_s* plan, const void* h16, const void* a16_cur, void* a16_next,
+                             float* A, float* m, float* v, int optimizer, int64_t t, double lr, double b1,
+                             double b2, double eps, int32_t* status, cudaStream_t st);
 
 }  // namespace sos

@@ -137,7 +137,9 @@ residual_kernel(const T* __restrict__ c, const T* __restrict__ p, T* __restrict_
     if (resid) resid += inst * M;
     loss += inst * 2;
     partials += inst * 2 * gridDim.x;
-    double sr = 0.0, sp = 0.0;
+    // Each thread sums its few (about M / (blocks * 256)) terms in T; the block
+    // and grid levels add in double.
+    T tr_t = T(0), tp_t = T(0);
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -145,9 +147,10 @@ residual_kernel(const T* __restrict__ c, const T* __restrict__ p, T* __restrict_
         const T e = cv - pv;
         if (resid) resid[i] = e;
         if (!finite_val(cv) || !finite_val(pv) || !finite_val(e)) bad = 1;
-        sr += (double)e * (double)e;
-        sp += (double)pv * (double)pv;
+        tr_t += e * e;
+        tp_t += pv * pv;
     }
+    double sr = (double)tr_t, sp = (double)tp_t;
     __shared__ double red_r[kThreads / 32], red_p[kThreads / 32];
     __shared__ int red_bad;
     __shared__ bool is_last;
@@ -262,32 +265,68 @@ simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const 
 }
 
 // ---- H(r) in bf16 for the tensor-core adjoint ----------------------------------------
-// Each thread writes 8 consecutive b of one row a with one 16-byte store.
+// H is symmetric (idx(a, b) = idx(b, a)), so each block reads the index table
+// and gathers the residual for one 64 x 64 tile on or above the diagonal and
+// writes both that tile and its transpose (through shared memory, so both
+// writes are row-contiguous).
 
-__global__ void build_h16_kernel(const float* __restrict__ resid, const int32_t* __restrict__ idx,
-                                 int64_t ld_idx, int64_t N, __nv_bfloat16* __restrict__ h, int64_t ldh) {
-    const int64_t chunks = (N + 7) / 8;
-    const int64_t total = N * chunks;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = i / chunks, b0 = (i - a * chunks) * 8;
-        const int32_t* irow = idx + a * ld_idx + b0;
-        __nv_bfloat16* hrow = h + a * ldh + b0;
-        if (b0 + 8 <= N) {
-            const int4 i0 = *reinterpret_cast<const int4*>(irow);
-            const int4 i1 = *reinterpret_cast<const int4*>(irow + 4);
-            __nv_bfloat162 v0 = __floats2bfloat162_rn(resid[i0.x], resid[i0.y]);
-            __nv_bfloat162 v1 = __floats2bfloat162_rn(resid[i0.z], resid[i0.w]);
-            __nv_bfloat162 v2 = __floats2bfloat162_rn(resid[i1.x], resid[i1.y]);
-            __nv_bfloat162 v3 = __floats2bfloat162_rn(resid[i1.z], resid[i1.w]);
-            uint4 out;
-            out.x = *reinterpret_cast<uint32_t*>(&v0);
-            out.y = *reinterpret_cast<uint32_t*>(&v1);
-            out.z = *reinterpret_cast<uint32_t*>(&v2);
-            out.w = *reinterpret_cast<uint32_t*>(&v3);
-            *reinterpret_cast<uint4*>(hrow) = out;
+__global__ void __launch_bounds__(kThreads)
+build_h16_kernel(const float* __restrict__ resid, const int32_t* __restrict__ idx, int64_t ld_idx, int64_t N,
+                 __nv_bfloat16* __restrict__ h, int64_t ldh) {
+    const int I = blockIdx.y, J = blockIdx.x;
+    if (J < I) return;
+    __shared__ float tileT[64][65];
+    const int64_t a0 = (int64_t)I * 64, b0 = (int64_t)J * 64;
+    const int cc = (threadIdx.x & 15) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int rr = (threadIdx.x >> 4) + 16 * k;
+        const int64_t a = a0 + rr, b = b0 + cc;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (a < N) {
+            const int32_t* irow = idx + a * ld_idx + b;
+            __nv_bfloat16* hrow = h + a * ldh + b;
+            if (b + 4 <= N) {
+                const int4 g = *reinterpret_cast<const int4*>(irow);
+                v[0] = resid[g.x];
+                v[1] = resid[g.y];
+                v[2] = resid[g.z];
+                v[3] = resid[g.w];
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+                __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+                uint2 out;
+                out.x = *reinterpret_cast<uint32_t*>(&lo);
+                out.y = *reinterpret_cast<uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(hrow) = out;
+            } else {
+                for (int j = 0; j < 4 && b + j < N; ++j) {
+                    v[j] = resid[irow[j]];
+                    hrow[j] = __float2bfloat16_rn(v[j]);
+                }
+            }
+        }
+        if (I != J) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tileT[cc + j][rr] = v[j];
+        }
+    }
+    if (I == J) return;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int rr = (threadIdx.x >> 4) + 16 * k;
+        const int64_t b = b0 + rr, a = a0 + cc;      // row b of H, columns a .. a+3
+        if (b >= N) continue;
+        __nv_bfloat16* hrow = h + b * ldh + a;
+        if (a + 4 <= N) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(tileT[rr][cc], tileT[rr][cc + 1]);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(tileT[rr][cc + 2], tileT[rr][cc + 3]);
+            uint2 out;
+            out.x = *reinterpret_cast<uint32_t*>(&lo);
+            out.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(hrow) = out;
         } else {
-            for (int64_t b = b0; b < N; ++b) hrow[b - b0] = __float2bfloat16_rn(resid[irow[b - b0]]);
+            for (int j = 0; j < 4 && a + j < N; ++j) hrow[j] = __float2bfloat16_rn(tileT[rr][cc + j]);
         }
     }
 }
@@ -410,11 +449,13 @@ int launch_simt_adjoint(const sos_plan_s* p, const T* A, const T* resid, T* grad
 }
 
 int launch_build_h16(const sos_plan_s* p, const float* resid, void* h16, cudaStream_t st) {
-    const int64_t work = p->N * ceil_div(p->N, 8);
+    const int64_t T = ceil_div(p->N, 64);
+    if (T > 65535) return fail(SOS_E_UNSUPPORTED, "build_h16: too many tiles");
+    dim3 grid((unsigned)T, (unsigned)T);
     {
         KernelScope ks_("build_h16", st);
-        build_h16_kernel<<<grid_for(work, p->dev.num_sms * 8), kThreads, 0, st>>>(
-            resid, p->dev.idx, p->ld_idx, p->N, (__nv_bfloat16*)h16, p->ld16h);
+        build_h16_kernel<<<grid, kThreads, 0, st>>>(resid, p->dev.idx, p->ld_idx, p->N, (__nv_bfloat16*)h16,
+                                                    p->ld16h);
     }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;

@@ -18,6 +18,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -29,14 +31,26 @@ constexpr int A_BYTES = BM * BK * 2;             // 16 KB
 constexpr int B_BYTES = BN * BK * 2;             // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 48 KB
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
+constexpr int EPI_WARPS = 4;
+constexpr int EPI_STAGE_BYTES = EPI_WARPS * 32 * 33 * 4;   // transposition buffers
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EPI_STAGE_BYTES;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait, then give up
 
 // ---- epilogues ---------------------------------------------------------------
+//
+// The epilogue warps read the accumulator 32 x 32 at a time: warp q (= warp % 4)
+// owns rows 32q .. 32q+31 of the 128-row tile, and each tcgen05.ld gives lane i
+// row 32q+i, 32 consecutive columns.  The block is transposed through padded
+// shared memory (stage[i * 33 + j] = row i, column j) so that an epilogue works
+// with lane j = column j and walks the 32 rows: every global load and store of
+// a row segment is then one coalesced 128-byte access.
 
-// Forward: c[idx(a, b)] += w G_ab for b >= a.
+constexpr int STAGE_LD = 33;
+
+// Forward: c[idx(a, b)] += w G_ab for b >= a (w = 1 on the diagonal, 2 above).
+// All 32 index loads are issued before the first atomic, so they overlap.
 struct SegmentSumEpilogue {
     static constexpr const char* kName = "tc_forward";
     int N;
@@ -44,28 +58,22 @@ struct SegmentSumEpilogue {
     int64_t ld_idx;
     float* c;
 
-    __device__ __forceinline__ void operator()(int2 tile, int row_in_tile, int ch, const uint32_t (&v)[32]) const {
-        const int a = tile.x * BM + row_in_tile;
-        const int b0 = tile.y * BN + ch * 32;
-        if (a >= N || b0 >= N || b0 + 31 < a) return;
-        const int32_t* irow = idx + (int64_t)a * ld_idx + b0;
-        if (b0 + 32 <= N && b0 >= a + 1) {   // whole chunk valid and strictly above the diagonal
+    __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
+        if (a0 >= N || b0 >= N || b0 + 31 < a0) return;
+        const int b = b0 + lane;
+        if (b >= N) return;
+        const int32_t* col = idx + (int64_t)a0 * ld_idx + b;
+        int32_t g[32];
 #pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-                const int4 g = *reinterpret_cast<const int4*>(irow + 4 * j4);
-                atomicAdd(c + g.x, 2.0f * __uint_as_float(v[4 * j4 + 0]));
-                atomicAdd(c + g.y, 2.0f * __uint_as_float(v[4 * j4 + 1]));
-                atomicAdd(c + g.z, 2.0f * __uint_as_float(v[4 * j4 + 2]));
-                atomicAdd(c + g.w, 2.0f * __uint_as_float(v[4 * j4 + 3]));
-            }
-        } else {
+        for (int i = 0; i < 32; ++i) {
+            const int a = a0 + i;
+            g[i] = (a < N && a <= b) ? __ldg(col + (int64_t)i * ld_idx) : -1;
+        }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int b = b0 + j;
-                if (b >= a && b < N) {
-                    const float g = __uint_as_float(v[j]);
-                    atomicAdd(c + irow[j], b == a ? g : 2.0f * g);
-                }
+        for (int i = 0; i < 32; ++i) {
+            if (g[i] >= 0) {
+                const float v = stage[i * STAGE_LD + lane];
+                atomicAdd(c + g[i], a0 + i == b ? v : 2.0f * v);
             }
         }
     }
@@ -79,19 +87,78 @@ struct StoreEpilogue {
     float scale;
     float* out;
 
-    __device__ __forceinline__ void operator()(int2 tile, int row_in_tile, int ch, const uint32_t (&v)[32]) const {
-        const int a = tile.x * BM + row_in_tile;
-        const int k0 = tile.y * BN + ch * 32;
-        if (a >= rows || k0 >= cols) return;
-        float* orow = out + (int64_t)a * ld + k0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (k0 + j < cols) orow[j] = scale * __uint_as_float(v[j]);
+    __device__ __forceinline__ void operator()(int a0, int k0, const float* stage, int lane) const {
+        const int k = k0 + lane;
+        if (a0 >= rows || k >= cols) return;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const int a = a0 + i;
+            if (a >= rows) break;
+            out[(int64_t)a * ld + k] = scale * stage[i * STAGE_LD + lane];
+        }
     }
 };
 
 struct DiagEpilogue : StoreEpilogue {
     static constexpr const char* kName = "tc_gemm_diag";
+};
+
+// Adjoint with the optimiser step fused in: grad = 2 acc, then gradient
+// descent or Adam on the FP32 master A (and m, v), and the bf16 copy of the
+// updated A written to the other buffer of the ping-pong pair (the current one
+// is still being read as an operand by other tiles).
+struct UpdateEpilogue {
+    static constexpr const char* kName = "tc_adjoint_update";
+    int rows, cols, optimizer;
+    float lr, b1, b2, eps, c1, c2;
+    float* A;
+    float* m;
+    float* v;
+    __nv_bfloat16* a16_next;
+    int64_t ld16;
+
+    // Processes the 32 rows in two halves; each half issues all its global
+    // loads before using any of them.
+    __device__ __forceinline__ void operator()(int a0, int k0, const float* stage, int lane) const {
+        const int k = k0 + lane;
+        if (a0 >= rows || k >= cols) return;
+        const float one = 1.0f;
+        const int nrows = rows - a0 < 32 ? rows - a0 : 32;
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
+            float x[16], mm[16], vv[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int64_t e = (int64_t)(a0 + h + i) * cols + k;
+                const bool ok = h + i < nrows;
+                x[i] = ok ? A[e] : 0.0f;
+                if (optimizer != SOS_GD) {
+                    mm[i] = ok ? m[e] : 0.0f;
+                    vv[i] = ok ? v[e] : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (h + i >= nrows) break;
+                const int64_t e = (int64_t)(a0 + h + i) * cols + k;
+                const float g = 2.0f * stage[(h + i) * STAGE_LD + lane];
+                float xi = x[i];
+                if (optimizer == SOS_GD) {
+                    xi -= lr * g;
+                } else {
+                    const float mi = b1 * mm[i] + (one - b1) * g;
+                    const float vi = b2 * vv[i] + (one - b2) * g * g;
+                    m[e] = mi;
+                    v[e] = vi;
+                    const float mhat = mi / c1;
+                    const float vhat = vi / c2;
+                    xi -= lr * mhat / (sqrtf(vhat) + eps);
+                }
+                A[e] = xi;
+                a16_next[(int64_t)(a0 + h + i) * ld16 + k] = __float2bfloat16_rn(xi);
+            }
+        }
+    }
 };
 
 // ---- the GEMM core ---------------------------------------------------------------
@@ -112,6 +179,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     uint64_t* drain = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile uint32_t* err = tmem_slot + 1;
+    float* epi_stage = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + BAR_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -239,12 +307,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             tc_fence_after();
             const int2 tile = tiles[t];
+            float* stage = epi_stage + (warp - 2) * 32 * STAGE_LD;
 #pragma unroll 1
             for (int ch = 0; ch < BN / 32; ++ch) {
                 uint32_t v[32];
                 tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
                 tmem_ld_wait();
-                epi(tile, q * 32 + lane, ch, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stage[lane * STAGE_LD + j] = __uint_as_float(v[j]);
+                __syncwarp();
+                epi(tile.x * BM + q * 32, tile.y * BN + ch * 32, stage, lane);
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -330,6 +403,32 @@ int launch_tc_adjoint(const sos_plan_s* p, const void* h16, const void* a16, flo
     SOS_CHECK(make_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
     SOS_CHECK(make_map(&mA, a16, p->r, p->N, p->ld16, 64, BK));
     StoreEpilogue epi{(int)p->N, (int)p->r, p->r, 2.0f, grad};
+    return launch_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles, p->dev.num_adj_tiles,
+                             p->dev.num_sms, epi, status, st);
+}
+
+int launch_tc_adjoint_update(const sos_plan_s* p, const void* h16, const void* a16_cur, void* a16_next, float* A,
+                             float* m, float* v, int optimizer, int64_t t, double lr, double b1, double b2,
+                             double eps, int32_t* status, cudaStream_t st) {
+    using namespace tc;
+    CUtensorMap mH, mA;
+    SOS_CHECK(make_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
+    SOS_CHECK(make_map(&mA, a16_cur, p->r, p->N, p->ld16, 64, BK));
+    UpdateEpilogue epi;
+    epi.rows = (int)p->N;
+    epi.cols = (int)p->r;
+    epi.optimizer = optimizer;
+    epi.lr = (float)lr;
+    epi.b1 = (float)b1;
+    epi.b2 = (float)b2;
+    epi.eps = (float)eps;
+    epi.c1 = (float)(1.0 - std::pow(b1, (double)t));
+    epi.c2 = (float)(1.0 - std::pow(b2, (double)t));
+    epi.A = A;
+    epi.m = m;
+    epi.v = v;
+    epi.a16_next = static_cast<__nv_bfloat16*>(a16_next);
+    epi.ld16 = p->ld16;
     return launch_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles, p->dev.num_adj_tiles,
                              p->dev.num_sms, epi, status, st);
 }

@@ -84,7 +84,7 @@ Workspace workspace_layout(const sos_plan_s* p, int prec) {
     w.resid = take((size_t)p->M * elt);
     w.grad = take((size_t)p->N * (size_t)p->r * elt);
     if (prec == SOS_BF16) {
-        w.a16 = take((size_t)p->N * (size_t)p->ld16 * 2);
+        w.a16 = take(2 * (size_t)p->N * (size_t)p->ld16 * 2);
         w.h16 = take((size_t)p->N * (size_t)p->ld16h * 2);
     }
     w.total = off;

@@ -223,3 +223,73 @@ def test_nonfinite_target_sets_status(prec):
     pl.loss_grad(torch.from_numpy(A).float().to(DEV), torch.from_numpy(p).float().to(DEV), prec)
     assert pl.status(prec) == L.SOS_E_NONFINITE
     assert pl.status(prec) == L.SOS_OK      # read-and-clear
+
+
+# -- the fused BF16 step (update inside the adjoint epilogue) --------------------------------
+
+@pytest.mark.parametrize("n,two_d,r", [(6, 8, 210), (7, 8, 130), (9, 6, 700)])
+def test_fused_bf16_gd_steps(n, two_d, r):
+    o, A, p = problem(n, two_d, r)
+    p32 = p.astype(np.float32).astype(np.float64)
+    pl = Plan(n, two_d, r)
+    A_dev = torch.from_numpy(A).float().to(DEV)
+    lr = 1e-4
+    opt = Optimizer(pl, A_dev, prec="bf16", optimizer="gd", lr=lr)
+    p_dev = torch.from_numpy(p32).float().to(DEV)
+    A_prev = A.astype(np.float32).astype(np.float64)
+    for step in range(3):
+        loss = opt.step(p_dev)[0].item()
+        A16 = bf16_round(A_prev)                 # what the contractions saw
+        loss_ref, resid = o.residual(o.coeffs(A16), p32)
+        assert abs(loss - loss_ref) <= 1e-5 * loss_ref, step
+        g_ref = o.grad_from_resid(A16, resid)
+        bound = (2.0 ** -8 + 4 * o.N * 2.0 ** -24) * o.grad_from_resid(np.abs(A16), np.abs(resid))
+        A_new = A_dev.double().cpu().numpy()
+        want = A_prev - lr * g_ref
+        assert np.all(np.abs(A_new - want) <= lr * bound + 4 * 2.0 ** -24 * np.abs(want) + 1e-30), step
+        A_prev = A_new                          # next step's loss: at bf16 of the updated A
+
+
+def test_fused_bf16_adam_moments():
+    o, A, p = problem(6, 8, 210)
+    p32 = p.astype(np.float32).astype(np.float64)
+    pl = Plan(6, 8, 210)
+    A_dev = torch.from_numpy(A).float().to(DEV)
+    opt = Optimizer(pl, A_dev, prec="bf16", optimizer="adam", lr=1e-3)
+    opt.step(torch.from_numpy(p32).float().to(DEV))
+    A16 = bf16_round(A.astype(np.float32).astype(np.float64))
+    _, resid = o.residual(o.coeffs(A16), p32)
+    g_ref = o.grad_from_resid(A16, resid)
+    bound = (2.0 ** -8 + 4 * o.N * 2.0 ** -24) * o.grad_from_resid(np.abs(A16), np.abs(resid))
+    m = opt.m.double().cpu().numpy()
+    v = opt.v.double().cpu().numpy()
+    f1 = float(np.float32(1) - np.float32(0.9))     # (1 - beta1) as the kernel forms it in FP32
+    f2 = float(np.float32(1) - np.float32(0.999))
+    assert np.all(np.abs(m - f1 * g_ref) <= f1 * bound * 1.001 + 1e-7 * np.abs(g_ref))
+    assert np.all(np.abs(np.sqrt(v / f2) - np.abs(g_ref)) <= bound * 1.001 + 1e-6 * np.abs(g_ref))
+
+
+@pytest.mark.parametrize("optimizer", ["adam", "gd"])
+def test_step_fp32_matches_oracle(optimizer):
+    o, A, p = problem(5, 6, 56)
+    A32 = A.astype(np.float32)
+    p32 = p.astype(np.float32)
+    pl = Plan(5, 6, 56)
+    A_dev = torch.from_numpy(A32.copy()).to(DEV)
+    opt = Optimizer(pl, A_dev, prec="fp32", optimizer=optimizer, lr=1e-3)
+    p_dev = torch.from_numpy(p32).to(DEV)
+    Aref = A32.astype(np.float64)
+    m, v = np.zeros_like(Aref), np.zeros_like(Aref)
+    for t in range(1, 4):
+        opt.step(p_dev)
+        _, g, _ = o.loss_grad(Aref, p32.astype(np.float64))
+        if optimizer == "adam":
+            o.adam_step(Aref, m, v, g, t, lr=1e-3)
+        else:
+            o.gd_step(Aref, g, 1e-3)
+        got = A_dev.double().cpu().numpy()
+        assert rel(got, Aref) < 1e-5
+        Aref = got.copy()                        # compare one step at a time
+        if optimizer == "adam":
+            m = opt.m.double().cpu().numpy().copy()
+            v = opt.v.double().cpu().numpy().copy()

@@ -42,7 +42,7 @@ def test_matches_allocating_path_on_two_calls(prec, dtype, tol):
         torch.cuda.synchronize()
         assert torch.equal(resid, c - p)
         np.testing.assert_allclose(loss[:, 0].cpu().numpy(), want_loss.cpu().numpy(), rtol=tol)
-        np.testing.assert_allclose(loss[:, 1].cpu().numpy(), want_pp.cpu().numpy(), rtol=1e-12)
+        np.testing.assert_allclose(loss[:, 1].cpu().numpy(), want_pp.cpu().numpy(), rtol=tol)
 
 
 def test_multiblock_problem_matches():
