@@ -199,6 +199,49 @@ int sos_certify(sos_plan_t plan, const void* A, int a_is_double, const double* p
                 double tol_rel, double* rel_out, int* verdict_out,
                 void* workspace, void* stream);
 
+/* ---- solver (synchronous) ----------------------------------------------- */
+
+typedef struct {
+    int optimizer;            /* sos_opt, all stages */
+    double lr_bf16, lr_fp32, lr_fp64;
+    double beta1, beta2, eps;
+    int64_t max_steps;        /* step budget of the BF16 + FP32 stages */
+    int64_t check_every;      /* evaluate the loss every K steps */
+    double switch_rel;        /* BF16 -> FP32 when ||c-p||/||p|| < switch_rel ... */
+    int64_t stall_checks;     /* ... or after this many checks without a 1% gain;
+                                 FP32 -> FP64 after as many */
+    int64_t fp64_steps;       /* step budget of the FP64 stage (0: none) */
+    double cert_tol;          /* certificate threshold (Sec. 3: about 1e-8) */
+    int start_prec;           /* SOS_BF16 (the ladder), SOS_FP32 (no BF16
+                                 stage) or SOS_FP64 (FP64 steps only) */
+} sos_solve_opts;
+
+typedef struct {
+    int verdict;              /* sos_verdict */
+    int64_t steps, steps_bf16, steps_fp32, steps_fp64;
+    double rel_start_fp64;    /* FP64 ||c-p||/||p|| at the start point */
+    double rel_at_switch;     /* BF16-evaluated relative residual at the switch */
+    double min_rel;           /* best relative residual checked in FP32 */
+    double min_rel_fp64;      /* best relative residual checked in FP64 */
+    double rel_resid_fp64;    /* certificate of the returned A */
+} sos_result;
+
+/* Defaults: Adam, lr 1e-2 in every stage, 20000 BF16+FP32 steps, checks
+ * every 50, switch at 1e-3 or 4 stalled checks, 2000 FP64 steps, tolerance
+ * 1e-8, start in BF16. */
+int sos_solve_opts_default(sos_solve_opts* opts);
+
+/* Minimises 1/2 ||c(A) - p||^2 from the start point A by the precision
+ * ladder: BF16 steps until the relative residual falls below switch_rel (or
+ * stalls), FP32 steps until they stall, FP64 steps on an FP64 copy of the
+ * best FP32 point, then the FP64 certificate of the best checked point
+ * (Sec. 3: success is the minimum error over the iterations).  The Adam
+ * state carries over between stages.  A: dev N x r double, start point in,
+ * best point out; p64: dev M double.  Allocates and frees its own buffers
+ * and synchronises `stream`. */
+int sos_solve(sos_plan_t plan, const double* p64, double* A, const sos_solve_opts* opts,
+              sos_result* out, void* stream);
+
 /* Diagnostic: a plain tcgen05 BF16 GEMM with FP32 output through the same
  * tile machinery as the two contractions.  D (dev m x n, row stride n) =
  * X (dev m x k bf16, row stride ldx) times Y^T (b_mn_major = 0: Y is n x k,

@@ -28,7 +28,8 @@ EXPORTS = [
     "sos_workspace_size", "sos_workspace_init", "sos_coeffs", "sos_loss_grad",
     "sos_workspace_size_batched", "sos_loss_grad_batched", "sos_step", "sos_read_status",
     "sos_certify", "sos_diag_gemm_bf16", "sos_launch_count", "sos_timing_enable",
-    "sos_timing_reset", "sos_timing_report", "sos_loss_from_coeffs_static", "sos_last_error",
+    "sos_timing_reset", "sos_timing_report", "sos_loss_from_coeffs_static", "sos_solve_opts_default",
+    "sos_solve", "sos_last_error",
 ]
 
 
@@ -46,6 +47,25 @@ class sos_step_opts(ctypes.Structure):
 class sos_state(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_void_p), ("v", ctypes.c_void_p),
                 ("t", ctypes.c_int64), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class sos_solve_opts(ctypes.Structure):
+    _fields_ = [("optimizer", ctypes.c_int), ("lr_bf16", ctypes.c_double), ("lr_fp32", ctypes.c_double),
+                ("lr_fp64", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("max_steps", ctypes.c_int64), ("check_every", ctypes.c_int64),
+                ("switch_rel", ctypes.c_double), ("stall_checks", ctypes.c_int64),
+                ("fp64_steps", ctypes.c_int64), ("cert_tol", ctypes.c_double), ("start_prec", ctypes.c_int)]
+
+
+class sos_result(ctypes.Structure):
+    _fields_ = [("verdict", ctypes.c_int), ("steps", ctypes.c_int64), ("steps_bf16", ctypes.c_int64),
+                ("steps_fp32", ctypes.c_int64), ("steps_fp64", ctypes.c_int64),
+                ("rel_start_fp64", ctypes.c_double), ("rel_at_switch", ctypes.c_double),
+                ("min_rel", ctypes.c_double), ("min_rel_fp64", ctypes.c_double),
+                ("rel_resid_fp64", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _lib = None
@@ -83,6 +103,8 @@ def lib(auto_build: bool = True):
         "sos_certify": [vp, vp, i32, vp, dbl, P(dbl), P(i32), vp, vp],
         "sos_diag_gemm_bf16": [i32, vp, vp, vp, i64, i64, i64, i64, i64, vp, vp],
         "sos_loss_from_coeffs_static": [i32, i64, i64, vp, vp, vp, vp, vp],
+        "sos_solve_opts_default": [P(sos_solve_opts)],
+        "sos_solve": [vp, vp, vp, P(sos_solve_opts), P(sos_result), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -211,3 +233,15 @@ def sos_timing_report() -> dict:
 
 def sos_loss_from_coeffs_static(prec, batch, M, c, p, resid, loss, stream) -> None:
     _check(lib().sos_loss_from_coeffs_static(prec, batch, M, c, p, resid, loss, stream))
+
+
+def sos_solve_opts_default() -> sos_solve_opts:
+    o = sos_solve_opts()
+    _check(lib().sos_solve_opts_default(ctypes.byref(o)))
+    return o
+
+
+def sos_solve(plan, p64, A, opts: sos_solve_opts, stream) -> sos_result:
+    r = sos_result()
+    _check(lib().sos_solve(plan, p64, A, ctypes.byref(opts), ctypes.byref(r), stream))
+    return r

@@ -118,6 +118,8 @@ int launch_update(int64_t N, int64_t r, T* A, T* m, T* v, const T* grad, int opt
                   int64_t ld16, cudaStream_t st);
 template <typename T>
 int launch_fill(T* x, int64_t count, T value, cudaStream_t st);
+template <typename Tin, typename Tout>
+int launch_convert(const Tin* x, Tout* y, int64_t count, cudaStream_t st);
 
 // ---- tensor-core kernels (kernels_tc.cu) ------------------------------------
 

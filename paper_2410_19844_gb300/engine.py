@@ -124,6 +124,21 @@ class Plan:
                              _stream_handle())
 
 
+def solve(plan: Plan, p64: torch.Tensor, A: torch.Tensor, **opts) -> dict:
+    """Runs sos_solve (the BF16 -> FP32 -> FP64 ladder) on A (float64, in place);
+    keyword arguments override fields of the default options."""
+    if A.dtype != torch.float64 or p64.dtype != torch.float64:
+        raise ValueError("A and p must be float64 device tensors")
+    o = L.sos_solve_opts_default()
+    for k, v in opts.items():
+        if k in ("optimizer",) and isinstance(v, str):
+            v = L.SOS_ADAM if v == "adam" else L.SOS_GD
+        if k == "start_prec" and isinstance(v, str):
+            v = L.PREC[v]
+        setattr(o, k, v)
+    return L.sos_solve(plan.handle, _ptr(p64), _ptr(A), o, _stream_handle()).as_dict()
+
+
 class Optimizer:
     """Adam (the paper's optimiser, Sec. 3) or GD state for one A, stepping
     through sos_step."""
