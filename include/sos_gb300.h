@@ -242,6 +242,62 @@ int sos_solve_opts_default(sos_solve_opts* opts);
 int sos_solve(sos_plan_t plan, const double* p64, double* A, const sos_solve_opts* opts,
               sos_result* out, void* stream);
 
+/* ---- groups: many small problems stepped together (serving) --------------- */
+
+/* A group steps up to `capacity` independent problems, each with its own plan
+ * (any n, 2d; r must equal N) and buffers, FP32 or FP64 on CUDA cores.  One
+ * group step runs four kernels whose work lists cover every active problem
+ * (64 x 64 tiles of every A A^T, coefficient chunks, tiles of every 2 H A with
+ * the optimiser update fused), so large and small problems share the GPU.
+ * No result depends on which other problems share the group: a problem's
+ * iterates are bitwise the same alone or in a mix.  The optimiser (and beta1,
+ * beta2, eps) is fixed per group; the step size per problem. */
+typedef struct sos_group_s* sos_group_t;
+
+int sos_group_create(int prec, int capacity, int optimizer, double beta1, double beta2,
+                     double eps, sos_group_t* out);
+int sos_group_destroy(sos_group_t group);
+
+/* Device scratch one problem of this plan needs in a group of precision prec
+ * (the second buffer of its A, its Gram matrix, residual and partial sums). */
+int sos_group_scratch_size(sos_plan_t plan, int prec, size_t* bytes);
+
+/* Puts a problem into slot `slot` (0 <= slot < capacity), starting from its
+ * current A: A, m, v dev N x r (zero m, v for a fresh Adam state), p dev M,
+ * scratch dev sos_group_scratch_size bytes; all caller-owned and kept alive
+ * until the slot is cleared.  t0 = optimiser steps already taken with this m,
+ * v (0 for a fresh state), so that Adam's bias correction continues.  The
+ * first call for a plan builds its device tables (allocates; do it before
+ * capturing).  Takes effect at the next sos_group_sync. */
+int sos_group_set(sos_group_t group, int slot, sos_plan_t plan, void* A, void* m, void* v,
+                  const void* p, void* scratch, double lr, int64_t t0);
+int sos_group_clear(sos_group_t group, int slot);
+
+/* Uploads the slot table and work lists after set/clear (stream-ordered;
+ * waits for the group's earlier work first). */
+int sos_group_sync(sos_group_t group, void* stream);
+
+/* Runs `steps` steps of every active problem as one CUDA graph (captured on
+ * first use for that step count, replayed after), ordered after the work
+ * already queued on `stream` and before work queued on it later. */
+int sos_group_run(sos_group_t group, int steps, void* stream);
+
+/* Host double[2 * capacity]: {1/2 ||c - p||^2, ||p||^2} of each slot at the
+ * last step (before its update); zeros for empty slots.  Synchronises. */
+int sos_group_losses(sos_group_t group, double* losses, void* stream);
+
+/* Where slot's iterates are: the update ping-pongs between A and the first
+ * region of the scratch, so A_current holds the latest iterate and
+ * A_previous the one before it -- the iterate whose loss the last step
+ * computed and sos_group_losses reports.  steps_taken counts the steps run
+ * in this group.  Any output may be NULL. */
+int sos_group_state(sos_group_t group, int slot, void** A_current, void** A_previous,
+                    int64_t* steps_taken);
+
+/* Element-wise copy with conversion between FP32 and FP64 (prec codes
+ * SOS_FP32 / SOS_FP64): y = x, count elements, dev, asynchronous. */
+int sos_convert(const void* x, int x_prec, void* y, int y_prec, int64_t count, void* stream);
+
 /* Diagnostic: a plain tcgen05 BF16 GEMM with FP32 output through the same
  * tile machinery as the two contractions.  D (dev m x n, row stride n) =
  * X (dev m x k bf16, row stride ldx) times Y^T (b_mn_major = 0: Y is n x k,

@@ -29,7 +29,9 @@ EXPORTS = [
     "sos_workspace_size_batched", "sos_loss_grad_batched", "sos_step", "sos_read_status",
     "sos_certify", "sos_diag_gemm_bf16", "sos_launch_count", "sos_timing_enable",
     "sos_timing_reset", "sos_timing_report", "sos_loss_from_coeffs_static", "sos_solve_opts_default",
-    "sos_solve", "sos_last_error",
+    "sos_solve", "sos_group_create", "sos_group_destroy", "sos_group_scratch_size", "sos_group_set",
+    "sos_group_clear", "sos_group_sync", "sos_group_run", "sos_group_losses", "sos_group_state",
+    "sos_convert", "sos_last_error",
 ]
 
 
@@ -105,6 +107,16 @@ def lib(auto_build: bool = True):
         "sos_loss_from_coeffs_static": [i32, i64, i64, vp, vp, vp, vp, vp],
         "sos_solve_opts_default": [P(sos_solve_opts)],
         "sos_solve": [vp, vp, vp, P(sos_solve_opts), P(sos_result), vp],
+        "sos_group_create": [i32, i32, i32, dbl, dbl, dbl, P(vp)],
+        "sos_group_destroy": [vp],
+        "sos_group_scratch_size": [vp, i32, P(ctypes.c_size_t)],
+        "sos_group_set": [vp, i32, vp, vp, vp, vp, vp, vp, dbl, i64],
+        "sos_group_clear": [vp, i32],
+        "sos_group_sync": [vp, vp],
+        "sos_group_run": [vp, i32, vp],
+        "sos_group_losses": [vp, vp, vp],
+        "sos_group_state": [vp, i32, P(vp), P(vp), P(i64)],
+        "sos_convert": [vp, i32, vp, i32, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -245,3 +257,50 @@ def sos_solve(plan, p64, A, opts: sos_solve_opts, stream) -> sos_result:
     r = sos_result()
     _check(lib().sos_solve(plan, p64, A, ctypes.byref(opts), ctypes.byref(r), stream))
     return r
+
+
+def sos_group_create(prec, capacity, optimizer, beta1=0.9, beta2=0.999, eps=1e-8) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sos_group_create(prec, capacity, optimizer, beta1, beta2, eps, ctypes.byref(h)))
+    return h.value
+
+
+def sos_group_destroy(group) -> None:
+    _check(lib().sos_group_destroy(group))
+
+
+def sos_group_scratch_size(plan, prec) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sos_group_scratch_size(plan, prec, ctypes.byref(b)))
+    return b.value
+
+
+def sos_group_set(group, slot, plan, A, m, v, p, scratch, lr, t0=0) -> None:
+    _check(lib().sos_group_set(group, slot, plan, A, m, v, p, scratch, lr, t0))
+
+
+def sos_group_clear(group, slot) -> None:
+    _check(lib().sos_group_clear(group, slot))
+
+
+def sos_group_sync(group, stream) -> None:
+    _check(lib().sos_group_sync(group, stream))
+
+
+def sos_group_run(group, steps, stream) -> None:
+    _check(lib().sos_group_run(group, steps, stream))
+
+
+def sos_group_losses(group, out_ptr, stream) -> None:
+    _check(lib().sos_group_losses(group, out_ptr, stream))
+
+
+def sos_group_state(group, slot):
+    """(pointer of the current A, pointer of the previous A, steps taken)."""
+    a, b, t = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+    _check(lib().sos_group_state(group, slot, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)))
+    return a.value, b.value, t.value
+
+
+def sos_convert(x, x_prec, y, y_prec, count, stream) -> None:
+    _check(lib().sos_convert(x, x_prec, y, y_prec, count, stream))

@@ -211,6 +211,20 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
     return SOS_OK;
 }
 
+int sos_convert(const void* x, int x_prec, void* y, int y_prec, int64_t count, void* stream) {
+    if (!x || !y || count < 0 || (x_prec != SOS_FP32 && x_prec != SOS_FP64) ||
+        (y_prec != SOS_FP32 && y_prec != SOS_FP64))
+        return fail(SOS_E_INVALID, "sos_convert: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (count == 0) return SOS_OK;
+    if (x_prec == y_prec) {
+        SOS_CUDA(cudaMemcpyAsync(y, x, (size_t)count * (x_prec == SOS_FP64 ? 8 : 4), cudaMemcpyDeviceToDevice, st));
+        return SOS_OK;
+    }
+    if (x_prec == SOS_FP64) return launch_convert<double, float>(static_cast<const double*>(x), static_cast<float*>(y), count, st);
+    return launch_convert<float, double>(static_cast<const float*>(x), static_cast<double*>(y), count, st);
+}
+
 int sos_read_status(sos_plan_t p, int prec, void* ws, void* stream) {
     if (!p || bad_prec(prec) || !ws) return fail(SOS_E_INVALID, "sos_read_status: bad argument");
     cudaStream_t st = (cudaStream_t)stream;

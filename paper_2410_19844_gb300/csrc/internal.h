@@ -74,6 +74,11 @@ struct DeviceTables {
     int2* adj_tiles = nullptr;  // (alpha block, column block) tiles of 2 H A
     int num_fwd_tiles = 0;
     int num_adj_tiles = 0;
+    // pair lists of the Gram identity, grouped by coefficient (built on demand):
+    // pairs of coefficient g are pair_pos[pair_ptr[g] .. pair_ptr[g+1]), each
+    // a * N + b with a <= b, the top bit set when a == b
+    int32_t* pair_ptr = nullptr;
+    int32_t* pair_pos = nullptr;
 };
 
 }  // namespace sos
@@ -95,6 +100,7 @@ namespace sos {
 
 Workspace workspace_layout(const sos_plan_s* plan, int prec);
 int ensure_device(sos_plan_s* plan);
+int ensure_pair_lists(sos_plan_s* plan);
 
 // ---- kernel launchers (kernels_simt.cu) ------------------------------------
 

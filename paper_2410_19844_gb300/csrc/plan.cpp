@@ -164,6 +164,8 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.idx);
         cudaFree(p->dev.fwd_tiles);
         cudaFree(p->dev.adj_tiles);
+        cudaFree(p->dev.pair_ptr);
+        cudaFree(p->dev.pair_pos);
         if (cur >= 0) cudaSetDevice(cur);
     }
     delete p;
@@ -284,6 +286,53 @@ int ensure_device(sos_plan_s* p) {
     t.num_fwd_tiles = (int)fwd.size();
     t.num_adj_tiles = (int)adj.size();
     p->dev = t;
+    return SOS_OK;
+}
+
+}  // namespace sos
+
+namespace sos {
+
+// Pair lists for gathering c_g = sum over pairs (a <= b, a + b = g) of
+// w_ab G_ab without atomics: a counting sort of the upper triangle of the
+// index table by coefficient.
+int ensure_pair_lists(sos_plan_s* p) {
+    SOS_CHECK(ensure_device(p));
+    std::lock_guard<std::mutex> lock(p->mu);
+    if (p->dev.pair_ptr) return SOS_OK;
+    if (p->N > 46340) return fail(SOS_E_UNSUPPORTED, "pair lists: N too large for 32-bit positions");
+    const int n = p->n, W = p->two_d + 1;
+    const int64_t N = p->N, M = p->M;
+    std::vector<int32_t> ptr(M + 1, 0);
+    auto rank = [&](int64_t a, int64_t b) {
+        int32_t g = 0;
+        for (int j = 0; j < n; ++j) g += p->phi[(size_t)j * W + p->Sd[a * n + j] + p->Sd[b * n + j]];
+        return g;
+    };
+    for (int64_t a = 0; a < N; ++a)
+        for (int64_t b = a; b < N; ++b) ptr[rank(a, b) + 1]++;
+    for (int64_t g = 0; g < M; ++g) ptr[g + 1] += ptr[g];
+    std::vector<int32_t> pos(ptr[M]);
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t a = 0; a < N; ++a)
+        for (int64_t b = a; b < N; ++b) {
+            const int32_t g = rank(a, b);
+            int32_t v = (int32_t)(a * N + b);
+            if (a == b) v |= INT32_MIN;
+            pos[fill[g]++] = v;
+        }
+    int32_t *d_ptr = nullptr, *d_pos = nullptr;
+    cudaError_t e = cudaMalloc(&d_ptr, ptr.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_pos, std::max<size_t>(1, pos.size()) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_pos, pos.data(), pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_ptr);
+        cudaFree(d_pos);
+        return cuda_fail(e, "pair lists: upload");
+    }
+    p->dev.pair_ptr = d_ptr;
+    p->dev.pair_pos = d_pos;
     return SOS_OK;
 }
 
