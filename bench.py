@@ -45,6 +45,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=4096)
+    ap.add_argument("--latency-requests", type=int, default=512)
+    ap.add_argument("--plain-sample", type=int, default=64)
     return ap.parse_args()
 
 
@@ -236,6 +240,67 @@ def config_of(w, world):
             "l2": "inputs exceed L2 (bf16 A 226 MB, bf16 H 226 MB, idx 451 MB); no flush"}
 
 
+# -- serving stream ------------------------------------------------------------------
+
+def run_serving(args):
+    """Served mixed stream vs one problem at a time through the single-problem path.
+
+    Requests: n uniform in {3..8}, 2d in {4, 6, 8}, r = N; even ids SOS (sum of
+    floor(N/2) random squares), odd ids made negative at a point.  Inputs are
+    built on the device before any timing.  Throughput: all requests offered at
+    once.  Latency (arrival -> verdict): Poisson arrivals at 0.5x and 1.5x the
+    plain path's measured capacity."""
+    import numpy as np
+    import torch
+
+    from paper_2410_19844_gb300 import _lib as L
+    from paper_2410_19844_gb300.server import Server, latency_stats, run_plain
+    from paper_2410_19844_gb300.workloads import build_jobs
+
+    jobs = build_jobs(args.serving_requests, 1.0, seed=0, arrivals=False)
+    sample = jobs[:args.plain_sample]
+    run_plain(sample[:4])                                    # warm-up (plans, graphs)
+    t0 = time.perf_counter()
+    plain = run_plain(sample)
+    t_plain = time.perf_counter() - t0
+    plain_rate = len(sample) / t_plain
+
+    srv = Server(capacity=512, steps_per_tick=32)
+    srv.run(jobs[:8])                                          # warm-up
+    srv_launch0 = srv.launches
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    served = srv.run(jobs)
+    t_served = time.perf_counter() - t0
+    launches = srv.launches - srv_launch0
+    served_rate = len(jobs) / t_served
+    by_rid = {v.rid: v for v in served}
+    agree = sum(by_rid[v.rid].verdict == v.verdict for v in plain)
+    counts = {"sos": 0, "not_converged": 0, "error": 0}
+    names = {L.SOS_VERDICT_SOS: "sos", L.SOS_VERDICT_NOT_CONVERGED: "not_converged", L.SOS_VERDICT_ERROR: "error"}
+    for v in served:
+        counts[names[v.verdict]] += 1
+    sos_ok = sum(1 for v in served if v.rid % 2 == 0 and v.verdict == L.SOS_VERDICT_SOS)
+    neg_ok = sum(1 for v in served if v.rid % 2 == 1 and v.verdict == L.SOS_VERDICT_NOT_CONVERGED)
+
+    latency = {}
+    for mult in (0.5, 1.5):
+        rate = mult * plain_rate
+        stream = build_jobs(args.latency_requests, rate, seed=1)
+        out = srv.run(stream)
+        st = latency_stats(out)
+        latency[f"{mult}x_plain"] = {"rate_per_s": rate, "requests": len(stream), **st}
+    srv.close()
+    return {"workload": "serving_n3-8_2d4-8", "requests": len(jobs), "served_verdicts_per_s": served_rate,
+            "served_s": t_served, "plain_verdicts_per_s": plain_rate, "plain_sample": len(sample),
+            "speedup_vs_plain": served_rate / plain_rate, "verdict_agreement_with_plain": f"{agree}/{len(sample)}",
+            "verdicts": counts, "sos_targets_certified": f"{sos_ok}/{(len(jobs) + 1) // 2}",
+            "negative_targets_not_converged": f"{neg_ok}/{len(jobs) // 2}",
+            "latency": latency, "slots": 512, "steps_per_tick": 32, "gpu_launches": launches,
+            "note": "grouped FP32 then FP64 (FP32 adjoint) steps, captured graphs of 32 steps; "
+                    "plain = sos_step launches per problem, one problem at a time, same decision rule"}
+
+
 # -- our arm -------------------------------------------------------------------------
 
 def run_ours(args):
@@ -369,12 +434,16 @@ def run_ours(args):
         v, desc, cores = oracle_sample(w)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(args)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
                 "config": config_of(w, world), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "cpu_baseline": cpu, "serving": serving,
                 "step": {"alg_tflops": step_tflops,
                          "frac_of_sustained": step_tflops / peaks["bf16_tflops_sustained"],
                          "frac_of_burst": step_tflops / peaks["bf16_tflops"],

@@ -254,8 +254,15 @@ int sos_solve(sos_plan_t plan, const double* p64, double* A, const sos_solve_opt
  * beta2, eps) is fixed per group; the step size per problem. */
 typedef struct sos_group_s* sos_group_t;
 
+/* flags: SOS_GROUP_FP32_ADJOINT (FP64 groups only) contracts the adjoint
+ * 2 H(r) A in FP32 from the FP64 residual and iterate; the forward, the
+ * residual, the loss and the update stay in FP64, so the certificate is
+ * still an FP64 evaluation.  It takes two thirds of the FP64 work off the
+ * step; the gradient it gives is accurate to FP32 relative to its own size. */
+#define SOS_GROUP_FP32_ADJOINT 1
+
 int sos_group_create(int prec, int capacity, int optimizer, double beta1, double beta2,
-                     double eps, sos_group_t* out);
+                     double eps, int flags, sos_group_t* out);
 int sos_group_destroy(sos_group_t group);
 
 /* Device scratch one problem of this plan needs in a group of precision prec
@@ -272,6 +279,9 @@ int sos_group_scratch_size(sos_plan_t plan, int prec, size_t* bytes);
 int sos_group_set(sos_group_t group, int slot, sos_plan_t plan, void* A, void* m, void* v,
                   const void* p, void* scratch, double lr, int64_t t0);
 int sos_group_clear(sos_group_t group, int slot);
+
+/* Changes the step size of an active slot (from the next sos_group_sync). */
+int sos_group_set_lr(sos_group_t group, int slot, double lr);
 
 /* Uploads the slot table and work lists after set/clear (stream-ordered;
  * waits for the group's earlier work first). */

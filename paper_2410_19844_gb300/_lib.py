@@ -31,7 +31,7 @@ EXPORTS = [
     "sos_timing_reset", "sos_timing_report", "sos_loss_from_coeffs_static", "sos_solve_opts_default",
     "sos_solve", "sos_group_create", "sos_group_destroy", "sos_group_scratch_size", "sos_group_set",
     "sos_group_clear", "sos_group_sync", "sos_group_run", "sos_group_losses", "sos_group_state",
-    "sos_convert", "sos_last_error",
+    "sos_convert", "sos_group_set_lr", "sos_last_error",
 ]
 
 
@@ -107,11 +107,12 @@ def lib(auto_build: bool = True):
         "sos_loss_from_coeffs_static": [i32, i64, i64, vp, vp, vp, vp, vp],
         "sos_solve_opts_default": [P(sos_solve_opts)],
         "sos_solve": [vp, vp, vp, P(sos_solve_opts), P(sos_result), vp],
-        "sos_group_create": [i32, i32, i32, dbl, dbl, dbl, P(vp)],
+        "sos_group_create": [i32, i32, i32, dbl, dbl, dbl, i32, P(vp)],
         "sos_group_destroy": [vp],
         "sos_group_scratch_size": [vp, i32, P(ctypes.c_size_t)],
         "sos_group_set": [vp, i32, vp, vp, vp, vp, vp, vp, dbl, i64],
         "sos_group_clear": [vp, i32],
+        "sos_group_set_lr": [vp, i32, dbl],
         "sos_group_sync": [vp, vp],
         "sos_group_run": [vp, i32, vp],
         "sos_group_losses": [vp, vp, vp],
@@ -259,9 +260,12 @@ def sos_solve(plan, p64, A, opts: sos_solve_opts, stream) -> sos_result:
     return r
 
 
-def sos_group_create(prec, capacity, optimizer, beta1=0.9, beta2=0.999, eps=1e-8) -> int:
+SOS_GROUP_FP32_ADJOINT = 1
+
+
+def sos_group_create(prec, capacity, optimizer, beta1=0.9, beta2=0.999, eps=1e-8, flags=0) -> int:
     h = ctypes.c_void_p()
-    _check(lib().sos_group_create(prec, capacity, optimizer, beta1, beta2, eps, ctypes.byref(h)))
+    _check(lib().sos_group_create(prec, capacity, optimizer, beta1, beta2, eps, flags, ctypes.byref(h)))
     return h.value
 
 
@@ -304,3 +308,7 @@ def sos_group_state(group, slot):
 
 def sos_convert(x, x_prec, y, y_prec, count, stream) -> None:
     _check(lib().sos_convert(x, x_prec, y, y_prec, count, stream))
+
+
+def sos_group_set_lr(group, slot, lr) -> None:
+    _check(lib().sos_group_set_lr(group, slot, lr))

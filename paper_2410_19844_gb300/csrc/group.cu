@@ -162,13 +162,16 @@ group_residual(const int* __restrict__ counts, const Item* __restrict__ items, i
     }
 }
 
-template <typename T>
+// Tc is the type of the contraction (T, or float for an FP64 group that
+// takes its gradient from the FP64 residual in FP32 arithmetic); the update
+// and the iterate stay in T.
+template <typename T, typename Tc>
 __global__ void __launch_bounds__(kT)
 group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, int cap,
               const Inst<T>* __restrict__ insts, const long long* __restrict__ step, int optimizer, double b1,
               double b2, double eps) {
-    __shared__ T Hs[16][64];
-    __shared__ T Bs[16][64];
+    __shared__ Tc Hs[16][64];
+    __shared__ Tc Bs[16][64];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int n_items = counts[2];
     const long long now = *step;
@@ -180,11 +183,11 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
         const T* A = (taken & 1) ? in.A1 : in.A0;
         T* A_next = (taken & 1) ? in.A0 : in.A1;
         const int row0 = it.i * 64, col0 = it.j * 64;
-        T acc[4][4];
+        Tc acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+            for (int j = 0; j < 4; ++j) acc[i][j] = Tc(0);
         for (int b0 = 0; b0 < N; b0 += 16) {
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
@@ -192,18 +195,18 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
                 {
                     const int rr = e >> 4, kk = e & 15;
                     const int a = row0 + rr, b = b0 + kk;
-                    Hs[kk][rr] = (a < N && b < N) ? in.resid[in.idx[(int64_t)a * in.ld_idx + b]] : T(0);
+                    Hs[kk][rr] = (a < N && b < N) ? (Tc)in.resid[in.idx[(int64_t)a * in.ld_idx + b]] : Tc(0);
                 }
                 {
                     const int kk = e >> 6, cc = e & 63;
                     const int b = b0 + kk, k = col0 + cc;
-                    Bs[kk][cc] = (b < N && k < r) ? A[(int64_t)b * r + k] : T(0);
+                    Bs[kk][cc] = (b < N && k < r) ? (Tc)A[(int64_t)b * r + k] : Tc(0);
                 }
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < 16; ++kk) {
-                T a[4], b[4];
+                Tc a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = Hs[kk][ty + 16 * i];
 #pragma unroll
@@ -227,7 +230,7 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
                 const int k = col0 + tx + 16 * j;
                 if (k >= r) continue;
                 const int64_t e = (int64_t)a * r + k;
-                const T g = T(2) * acc[i][j];
+                const T g = T(2) * (T)acc[i][j];
                 T x = A[e];
                 if (optimizer == SOS_GD) {
                     x -= lr * g;
@@ -289,6 +292,7 @@ using namespace sos::grp;
 
 struct sos_group_s {
     int prec = SOS_FP32;
+    bool fp32_adjoint = false;    // FP64 group: contraction of the adjoint in FP32
     int capacity = 0;
     int optimizer = SOS_ADAM;
     double b1 = 0.9, b2 = 0.999, eps = 1e-8;
@@ -395,8 +399,12 @@ int launch_step(sos_group_s* g, cudaStream_t st) {
     }
     {
         KernelScope ks_("group_adjoint", st);
-        group_adjoint<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
-                                                 g->optimizer, g->b1, g->b2, g->eps);
+        if (g->fp32_adjoint)
+            group_adjoint<T, float><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
+                                                            g->optimizer, g->b1, g->b2, g->eps);
+        else
+            group_adjoint<T, T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
+                                                        g->optimizer, g->b1, g->b2, g->eps);
     }
     {
         KernelScope ks_("group_advance", st);
@@ -418,14 +426,15 @@ int sos_group_scratch_size(sos_plan_t p, int prec, size_t* bytes) {
     return SOS_OK;
 }
 
-int sos_group_create(int prec, int capacity, int optimizer, double beta1, double beta2, double eps,
+int sos_group_create(int prec, int capacity, int optimizer, double beta1, double beta2, double eps, int flags,
                      sos_group_t* out) {
     if (!out || (prec != SOS_FP32 && prec != SOS_FP64) || capacity < 1 || capacity > (1 << 20) ||
-        (optimizer != SOS_ADAM && optimizer != SOS_GD))
+        (optimizer != SOS_ADAM && optimizer != SOS_GD) || (flags & ~SOS_GROUP_FP32_ADJOINT))
         return fail(SOS_E_INVALID, "sos_group_create: bad argument");
     *out = nullptr;
     sos_group_s* g = new sos_group_s();
     g->prec = prec;
+    g->fp32_adjoint = prec == SOS_FP64 && (flags & SOS_GROUP_FP32_ADJOINT);
     g->capacity = capacity;
     g->optimizer = optimizer;
     g->b1 = beta1;
@@ -486,6 +495,14 @@ int sos_group_set(sos_group_t g, int slot, sos_plan_t plan, void* A, void* m, vo
     s.lr = lr;
     s.join = g->steps;
     s.t0 = t0 < 0 ? 0 : t0;
+    g->dirty = true;
+    return SOS_OK;
+}
+
+int sos_group_set_lr(sos_group_t g, int slot, double lr) {
+    if (!g || slot < 0 || slot >= g->capacity || !g->slots[slot].active)
+        return fail(SOS_E_INVALID, "sos_group_set_lr: bad slot");
+    g->slots[slot].lr = lr;
     g->dirty = true;
     return SOS_OK;
 }

@@ -206,16 +206,36 @@ residual_kernel(const T* __restrict__ c, const T* __restrict__ p, T* __restrict_
         }
     }
     __syncthreads();
-    if (is_last && threadIdx.x == 0) {
+    if (is_last) {
+        // The last block adds the per-block partials: each thread a fixed
+        // stride of blocks, then the same warp and block tree as above, so the
+        // order never depends on which block finished last.
         __threadfence();
         double tr = 0.0, tp = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            tr += ((volatile double*)partials)[2 * b];
-            tp += ((volatile double*)partials)[2 * b + 1];
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+            tr += __ldcg(partials + 2 * b);
+            tp += __ldcg(partials + 2 * b + 1);
         }
-        loss[0] = 0.5 * tr;
-        loss[1] = tp;
-        counter[inst] = 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            tr += __shfl_down_sync(0xffffffffu, tr, o);
+            tp += __shfl_down_sync(0xffffffffu, tp, o);
+        }
+        __syncthreads();
+        if (lane == 0) {
+            red_r[warp] = tr;
+            red_p[warp] = tp;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sr2 = 0.0, sp2 = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                sr2 += red_r[w];
+                sp2 += red_p[w];
+            }
+            loss[0] = 0.5 * sr2;
+            loss[1] = sp2;
+            counter[inst] = 0;
+        }
     }
 }
 

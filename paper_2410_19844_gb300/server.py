@@ -72,6 +72,8 @@ class _Active:
     steps64: int = 0
     footprint: int = 0
     fresh: bool = False
+    lr: float = 0.0
+    decays: int = 0
 
 
 @dataclass
@@ -79,9 +81,11 @@ class Policy:
     lr32: float = 1e-2
     lr64: float = 1e-2
     cert_tol: float = 1e-8
-    switch_rel: float = 1e-6         # FP32 -> FP64 at once below this
+    switch_rel: float = 1e-7         # FP32 -> FP64 at once below this
     promote_rel: float = 1e-3        # ... or, when FP32 stalls, only below this
     stall_checks: int = 3            # checks without a 1% gain
+    decay: float = 0.1               # on a stall above target, scale the step size by this ...
+    max_decays: int = 2              # ... at most this many times per stage before deciding
     max_fp32_steps: int = 8000
     max_fp64_steps: int = 3000
 
@@ -93,14 +97,15 @@ def _footprint(plan: Plan, elt: int) -> int:
 
 class Server:
     def __init__(self, capacity: int = 256, hbm_budget: int = 16 << 30, steps_per_tick: int = 32,
-                 policy: Optional[Policy] = None, optimizer: str = "adam"):
+                 policy: Optional[Policy] = None, optimizer: str = "adam", fp32_adjoint: bool = True):
         self.capacity = capacity
         self.budget = hbm_budget
         self.K = steps_per_tick
         self.policy = policy or Policy()
         opt = L.SOS_ADAM if optimizer == "adam" else L.SOS_GD
         self.g32 = L.sos_group_create(L.SOS_FP32, capacity, opt)
-        self.g64 = L.sos_group_create(L.SOS_FP64, capacity, opt)
+        self.g64 = L.sos_group_create(L.SOS_FP64, capacity, opt,
+                                      flags=L.SOS_GROUP_FP32_ADJOINT if fp32_adjoint else 0)
         self.plans: dict = {}
         self.free32 = list(range(capacity))[::-1]
         self.free64 = list(range(capacity))[::-1]
@@ -155,7 +160,7 @@ class Server:
                         _ptr(b["p32"]), _ptr(b["s32"]), self.policy.lr32, 0)
         self.used += need
         self.peak_used = max(self.peak_used, self.used)
-        a = _Active(job, plan, slot, "fp32", b, footprint=need)
+        a = _Active(job, plan, slot, "fp32", b, footprint=need, lr=self.policy.lr32)
         self.active32[slot] = a
         return a
 
@@ -178,9 +183,10 @@ class Server:
                                device="cuda")
         self._release32(a)
         slot = self.free64.pop()
+        a.lr = self.policy.lr64 * (a.lr / self.policy.lr32)    # keep the FP32 stage's decays
         L.sos_group_set(self.g64, slot, a.plan.handle, _ptr(b["A64"]), _ptr(b["m64"]), _ptr(b["v64"]),
-                        _ptr(b["p64"]), _ptr(b["s64"]), self.policy.lr64, a.steps32)
-        a.slot, a.phase, a.fresh = slot, "fp64", True
+                        _ptr(b["p64"]), _ptr(b["s64"]), a.lr, a.steps32)
+        a.slot, a.phase, a.fresh, a.decays = slot, "fp64", True, 0
         a.stall, a.last_gain = 0, float("inf")
         self.used += need
         a.footprint += need
@@ -258,6 +264,11 @@ class Server:
                 stalled = a.stall >= pol.stall_checks or a.steps32 >= pol.max_fp32_steps
                 if rel <= pol.switch_rel or (stalled and rel <= pol.promote_rel):
                     self._promote(a)          # waits for a FP64 slot if none is free
+                elif stalled and a.decays < pol.max_decays and a.steps32 < pol.max_fp32_steps:
+                    a.decays += 1
+                    a.lr *= pol.decay
+                    a.stall, a.last_gain = 0, rel
+                    L.sos_group_set_lr(self.g32, slot, a.lr)
                 elif stalled:
                     self._retire(a, L.SOS_VERDICT_NOT_CONVERGED, rel, now, out)
             for slot, a in list(self.active64.items()):
@@ -278,6 +289,12 @@ class Server:
                 if rel <= pol.cert_tol:
                     # the iterate whose FP64 residual this is sits in the other buffer
                     self._retire(a, L.SOS_VERDICT_SOS, rel, now, out)
+                elif (a.stall >= pol.stall_checks and a.decays < pol.max_decays
+                      and a.steps64 < pol.max_fp64_steps):
+                    a.decays += 1
+                    a.lr *= pol.decay
+                    a.stall, a.last_gain = 0, rel
+                    L.sos_group_set_lr(self.g64, slot, a.lr)
                 elif a.stall >= pol.stall_checks or a.steps64 >= pol.max_fp64_steps:
                     self._retire(a, L.SOS_VERDICT_NOT_CONVERGED, rel, now, out)
         torch.cuda.synchronize()
@@ -308,7 +325,7 @@ def run_plain(jobs: list, policy: Optional[Policy] = None, K: int = 32, plans: O
         L.sos_convert(_ptr(A0), L.SOS_FP64, _ptr(A32), L.SOS_FP32, N * N, st)
         opt = Optimizer(plan, A32, prec="fp32", optimizer="adam", lr=pol.lr32)
         verdict, rel, s32, s64 = None, float("nan"), 0, 0
-        last_gain, stall = float("inf"), 0
+        last_gain, stall, decays = float("inf"), 0, 0
         promote = False
         while True:
             for _ in range(K):
@@ -327,17 +344,23 @@ def run_plain(jobs: list, policy: Optional[Policy] = None, K: int = 32, plans: O
             if rel <= pol.switch_rel or (stalled and rel <= pol.promote_rel):
                 promote = True
                 break
+            if stalled and decays < pol.max_decays and s32 < pol.max_fp32_steps:
+                decays += 1
+                opt.opts.lr *= pol.decay
+                stall, last_gain = 0, rel
+                continue
             if stalled:
                 verdict = L.SOS_VERDICT_NOT_CONVERGED
                 break
         if promote:
             A64 = torch.empty(N, N, dtype=torch.float64, device="cuda")
             L.sos_convert(_ptr(A32), L.SOS_FP32, _ptr(A64), L.SOS_FP64, N * N, st)
-            opt64 = Optimizer(plan, A64, prec="fp64", optimizer="adam", lr=pol.lr64)
+            opt64 = Optimizer(plan, A64, prec="fp64", optimizer="adam",
+                              lr=pol.lr64 * opt.opts.lr / pol.lr32)
             L.sos_convert(_ptr(opt.m), L.SOS_FP32, _ptr(opt64.m), L.SOS_FP64, N * N, st)
             L.sos_convert(_ptr(opt.v), L.SOS_FP32, _ptr(opt64.v), L.SOS_FP64, N * N, st)
             opt64.state.t = opt.state.t
-            last_gain, stall = float("inf"), 0
+            last_gain, stall, decays64 = float("inf"), 0, 0
             while True:
                 for _ in range(K):
                     opt64.step(p64)
@@ -351,6 +374,11 @@ def run_plain(jobs: list, policy: Optional[Policy] = None, K: int = 32, plans: O
                     last_gain, stall = rel, 0
                 else:
                     stall += 1
+                if stall >= pol.stall_checks and decays64 < pol.max_decays and s64 < pol.max_fp64_steps:
+                    decays64 += 1
+                    opt64.opts.lr *= pol.decay
+                    stall, last_gain = 0, rel
+                    continue
                 if stall >= pol.stall_checks or s64 >= pol.max_fp64_steps:
                     verdict = L.SOS_VERDICT_NOT_CONVERGED
                     break

@@ -143,9 +143,10 @@ def request_generator(req: Request) -> np.ndarray:
     return rng(req.rid).standard_normal((N, max(1, N // 2)))
 
 
-def request_point(req: Request) -> np.ndarray:
-    """x0 ~ N(0, I_n) at which an odd request is made negative."""
-    return rng(10_000_019 + req.rid).standard_normal(req.n)
+def request_points(req: Request, count: int = 64) -> np.ndarray:
+    """Candidate points x0 ~ N(0, I_n) at which an odd request is made negative
+    (the first admissible one is used)."""
+    return rng(10_000_019 + req.rid).standard_normal((count, req.n))
 
 
 def request_init(req: Request, sigma: float = 0.1) -> np.ndarray:
