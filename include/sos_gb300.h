@@ -310,12 +310,14 @@ int sos_convert(const void* x, int x_prec, void* y, int y_prec, int64_t count, v
 
 /* Diagnostic: a plain tcgen05 BF16 GEMM with FP32 output through the same
  * tile machinery as the two contractions.  D (dev m x n, row stride n) =
- * X (dev m x k bf16, row stride ldx) times Y^T (b_mn_major = 0: Y is n x k,
- * row stride ldy) or times Y (b_mn_major = 1: Y is k x n, row stride ldy).
+ * X (dev m x k bf16, row stride ldx) times Y^T (mode bit 0 clear: Y is n x k,
+ * row stride ldy) or times Y (bit 0 set: Y is k x n, row stride ldy).  Mode
+ * bit 1 runs it on CTA pairs (cta_group::2), as the contractions do unless
+ * the environment variable SOS_CTA_PAIRS is 0.
  * Row strides must be multiples of 8 elements and the bases 16-byte
  * aligned.  status: dev int32, zero on entry; a timed-out wait sets it.
  * Synchronises `stream`. */
-int sos_diag_gemm_bf16(int b_mn_major, const void* X, const void* Y, float* D,
+int sos_diag_gemm_bf16(int mode, const void* X, const void* Y, float* D,
                        int64_t m, int64_t n, int64_t k, int64_t ldx, int64_t ldy,
                        int32_t* status, void* stream);
 

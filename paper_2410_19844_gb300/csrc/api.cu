@@ -36,7 +36,8 @@ int forward(sos_plan_s* p, int prec, const void* A, void* ws, cudaStream_t st, v
     if (prec == SOS_FP32) return launch_simt_forward<float, float>(p, static_cast<const float*>(A), c, 1, st);
     void* a16 = at<char>(ws, w.a16);
     SOS_CHECK(launch_cast_bf16(static_cast<const float*>(A), p->N, p->r, a16, p->ld16, st));
-    return launch_tc_forward(p, a16, c, at<int32_t>(ws, w.status), st);
+    return use_cta_pairs() ? launch_tc_forward_pair(p, a16, c, at<int32_t>(ws, w.status), st)
+                           : launch_tc_forward(p, a16, c, at<int32_t>(ws, w.status), st);
 }
 
 int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad, void* loss, void* ws,
@@ -64,7 +65,9 @@ int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad
                                           st);
     void* h16 = at<char>(ws, w.h16);
     SOS_CHECK(launch_build_h16(p, resid, h16, st));
-    return launch_tc_adjoint(p, h16, at<char>(ws, w.a16), static_cast<float*>(grad), status, st);
+    return use_cta_pairs()
+               ? launch_tc_adjoint_pair(p, h16, at<char>(ws, w.a16), static_cast<float*>(grad), status, st)
+               : launch_tc_adjoint(p, h16, at<char>(ws, w.a16), static_cast<float*>(grad), status, st);
 }
 
 Workspace batched_layout(const sos_plan_s* p, int prec, int64_t batch) {
@@ -183,15 +186,16 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         if (!(s->flags & SOS_STATE_BF16_CURRENT))
             SOS_CHECK(launch_cast_bf16(static_cast<const float*>(s->A), p->N, p->r, a16_cur, p->ld16, st));
         SOS_CUDA(cudaMemsetAsync(c, 0, (size_t)p->M * sizeof(float), st));
-        SOS_CHECK(launch_tc_forward(p, a16_cur, c, status, st));
+        SOS_CHECK(use_cta_pairs() ? launch_tc_forward_pair(p, a16_cur, c, status, st)
+                                  : launch_tc_forward(p, a16_cur, c, status, st));
         double* L = loss ? static_cast<double*>(loss) : at<double>(ws, w.loss);
         SOS_CHECK(launch_residual<float>(p, c, static_cast<const float*>(pv), resid, L, at<double>(ws, w.partials),
                                          status, 1, st));
         void* h16 = at<char>(ws, w.h16);
         SOS_CHECK(launch_build_h16(p, resid, h16, st));
-        SOS_CHECK(launch_tc_adjoint_update(p, h16, a16_cur, a16_next, static_cast<float*>(s->A),
-                                           static_cast<float*>(s->m), static_cast<float*>(s->v), o->optimizer, t,
-                                           o->lr, o->beta1, o->beta2, o->eps, status, st));
+        auto adj = use_cta_pairs() ? launch_tc_adjoint_update_pair : launch_tc_adjoint_update;
+        SOS_CHECK(adj(p, h16, a16_cur, a16_next, static_cast<float*>(s->A), static_cast<float*>(s->m),
+                      static_cast<float*>(s->v), o->optimizer, t, o->lr, o->beta1, o->beta2, o->eps, status, st));
         s->flags = SOS_STATE_BF16_CURRENT | (cur ? 0 : SOS_STATE_BF16_INDEX);
         s->t = t;
         return SOS_OK;

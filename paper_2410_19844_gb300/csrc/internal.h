@@ -74,6 +74,10 @@ struct DeviceTables {
     int2* adj_tiles = nullptr;  // (alpha block, column block) tiles of 2 H A
     int num_fwd_tiles = 0;
     int num_adj_tiles = 0;
+    int2* fwd_tiles2 = nullptr;  // the same in 256 x 256 tiles, for CTA pairs
+    int2* adj_tiles2 = nullptr;
+    int num_fwd_tiles2 = 0;
+    int num_adj_tiles2 = 0;
     // pair lists of the Gram identity, grouped by coefficient (built on demand):
     // pairs of coefficient g are pair_pos[pair_ptr[g] .. pair_ptr[g+1]), each
     // a * N + b with a <= b, the top bit set when a == b
@@ -136,5 +140,18 @@ int launch_tc_adjoint(const sos_plan_s* plan, const void* h16, const void* a16, 
 int launch_tc_adjoint_update(const sos_plan_s* plan, const void* h16, const void* a16_cur, void* a16_next,
                              float* A, float* m, float* v, int optimizer, int64_t t, double lr, double b1,
                              double b2, double eps, int32_t* status, cudaStream_t st);
+
+// ---- the same on CTA pairs (kernels_tc2.cu) ---------------------------------------
+
+int launch_tc_forward_pair(const sos_plan_s* plan, const void* a16, float* c, int32_t* status, cudaStream_t st);
+int launch_tc_adjoint_pair(const sos_plan_s* plan, const void* h16, const void* a16, float* grad,
+                           int32_t* status, cudaStream_t st);
+int launch_tc_adjoint_update_pair(const sos_plan_s* plan, const void* h16, const void* a16_cur, void* a16_next,
+                                  float* A, float* m, float* v, int optimizer, int64_t t, double lr, double b1,
+                                  double b2, double eps, int32_t* status, cudaStream_t st);
+
+// Whether the tensor-core contractions run on CTA pairs (environment variable
+// SOS_CTA_PAIRS = 0 or 1, read once; pairs by default).
+bool use_cta_pairs();
 
 }  // namespace sos

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "tc_epilogues.cuh"
 #include "tc_ptx.cuh"
 
 namespace sos {
@@ -37,129 +38,6 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EPI_STAGE_B
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait, then give up
-
-// ---- epilogues ---------------------------------------------------------------
-//
-// The epilogue warps read the accumulator 32 x 32 at a time: warp q (= warp % 4)
-// owns rows 32q .. 32q+31 of the 128-row tile, and each tcgen05.ld gives lane i
-// row 32q+i, 32 consecutive columns.  The block is transposed through padded
-// shared memory (stage[i * 33 + j] = row i, column j) so that an epilogue works
-// with lane j = column j and walks the 32 rows: every global load and store of
-// a row segment is then one coalesced 128-byte access.
-
-constexpr int STAGE_LD = 33;
-
-// Forward: c[idx(a, b)] += w G_ab for b >= a (w = 1 on the diagonal, 2 above).
-// All 32 index loads are issued before the first atomic, so they overlap.
-struct SegmentSumEpilogue {
-    static constexpr const char* kName = "tc_forward";
-    int N;
-    const int32_t* idx;
-    int64_t ld_idx;
-    float* c;
-
-    __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
-        if (a0 >= N || b0 >= N || b0 + 31 < a0) return;
-        const int b = b0 + lane;
-        if (b >= N) return;
-        const int32_t* col = idx + (int64_t)a0 * ld_idx + b;
-        int32_t g[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int a = a0 + i;
-            g[i] = (a < N && a <= b) ? __ldg(col + (int64_t)i * ld_idx) : -1;
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            if (g[i] >= 0) {
-                const float v = stage[i * STAGE_LD + lane];
-                atomicAdd(c + g[i], a0 + i == b ? v : 2.0f * v);
-            }
-        }
-    }
-};
-
-// Adjoint / diagnostic GEMM: out[row][col] = scale * acc.
-struct StoreEpilogue {
-    static constexpr const char* kName = "tc_adjoint";
-    int rows, cols;
-    int64_t ld;
-    float scale;
-    float* out;
-
-    __device__ __forceinline__ void operator()(int a0, int k0, const float* stage, int lane) const {
-        const int k = k0 + lane;
-        if (a0 >= rows || k >= cols) return;
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-            const int a = a0 + i;
-            if (a >= rows) break;
-            out[(int64_t)a * ld + k] = scale * stage[i * STAGE_LD + lane];
-        }
-    }
-};
-
-struct DiagEpilogue : StoreEpilogue {
-    static constexpr const char* kName = "tc_gemm_diag";
-};
-
-// Adjoint with the optimiser step fused in: grad = 2 acc, then gradient
-// descent or Adam on the FP32 master A (and m, v), and the bf16 copy of the
-// updated A written to the other buffer of the ping-pong pair (the current one
-// is still being read as an operand by other tiles).
-struct UpdateEpilogue {
-    static constexpr const char* kName = "tc_adjoint_update";
-    int rows, cols, optimizer;
-    float lr, b1, b2, eps, c1, c2;
-    float* A;
-    float* m;
-    float* v;
-    __nv_bfloat16* a16_next;
-    int64_t ld16;
-
-    // Processes the 32 rows in two halves; each half issues all its global
-    // loads before using any of them.
-    __device__ __forceinline__ void operator()(int a0, int k0, const float* stage, int lane) const {
-        const int k = k0 + lane;
-        if (a0 >= rows || k >= cols) return;
-        const float one = 1.0f;
-        const int nrows = rows - a0 < 32 ? rows - a0 : 32;
-#pragma unroll
-        for (int h = 0; h < 32; h += 16) {
-            float x[16], mm[16], vv[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int64_t e = (int64_t)(a0 + h + i) * cols + k;
-                const bool ok = h + i < nrows;
-                x[i] = ok ? A[e] : 0.0f;
-                if (optimizer != SOS_GD) {
-                    mm[i] = ok ? m[e] : 0.0f;
-                    vv[i] = ok ? v[e] : 0.0f;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if (h + i >= nrows) break;
-                const int64_t e = (int64_t)(a0 + h + i) * cols + k;
-                const float g = 2.0f * stage[(h + i) * STAGE_LD + lane];
-                float xi = x[i];
-                if (optimizer == SOS_GD) {
-                    xi -= lr * g;
-                } else {
-                    const float mi = b1 * mm[i] + (one - b1) * g;
-                    const float vi = b2 * vv[i] + (one - b2) * g * g;
-                    m[e] = mi;
-                    v[e] = vi;
-                    const float mhat = mi / c1;
-                    const float vhat = vi / c2;
-                    xi -= lr * mhat / (sqrtf(vhat) + eps);
-                }
-                A[e] = xi;
-                a16_next[(int64_t)(a0 + h + i) * ld16 + k] = __float2bfloat16_rn(xi);
-            }
-        }
-    }
-};
 
 // ---- the GEMM core ---------------------------------------------------------------
 
@@ -347,9 +225,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// bf16 matrix of `outer` rows x `inner` columns, row stride ld elements.
-static int make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
-                    uint32_t box_inner, uint32_t box_outer) {
+}  // namespace tc
+
+// bf16 matrix of `outer` rows x `inner` columns, row stride ld elements,
+// 128-byte swizzle, zero fill outside the matrix.
+int make_bf16_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+                  uint32_t box_inner, uint32_t box_outer) {
+    using namespace tc;
     auto fn = encode_fn();
     if (!fn) return fail(SOS_E_CUDA, "cuTensorMapEncodeTiled is unavailable");
     if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15))
@@ -364,6 +246,8 @@ static int make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t o
     if (r != CUDA_SUCCESS) return fail(SOS_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return SOS_OK;
 }
+
+namespace tc {
 
 template <bool B_MN, class Epi>
 static int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
@@ -389,8 +273,8 @@ static int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, co
 int launch_tc_forward(const sos_plan_s* p, const void* a16, float* c, int32_t* status, cudaStream_t st) {
     using namespace tc;
     CUtensorMap mA, mB;
-    SOS_CHECK(make_map(&mA, a16, p->r, p->N, p->ld16, BK, BM));
-    SOS_CHECK(make_map(&mB, a16, p->r, p->N, p->ld16, BK, BN));
+    SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, BK, BM));
+    SOS_CHECK(make_bf16_map(&mB, a16, p->r, p->N, p->ld16, BK, BN));
     SegmentSumEpilogue epi{(int)p->N, p->dev.idx, p->ld_idx, c};
     return launch_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), p->dev.fwd_tiles, p->dev.num_fwd_tiles,
                               p->dev.num_sms, epi, status, st);
@@ -400,8 +284,8 @@ int launch_tc_adjoint(const sos_plan_s* p, const void* h16, const void* a16, flo
                       cudaStream_t st) {
     using namespace tc;
     CUtensorMap mH, mA;
-    SOS_CHECK(make_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
-    SOS_CHECK(make_map(&mA, a16, p->r, p->N, p->ld16, 64, BK));
+    SOS_CHECK(make_bf16_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
+    SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, 64, BK));
     StoreEpilogue epi{(int)p->N, (int)p->r, p->r, 2.0f, grad};
     return launch_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles, p->dev.num_adj_tiles,
                              p->dev.num_sms, epi, status, st);
@@ -412,8 +296,8 @@ int launch_tc_adjoint_update(const sos_plan_s* p, const void* h16, const void* a
                              double eps, int32_t* status, cudaStream_t st) {
     using namespace tc;
     CUtensorMap mH, mA;
-    SOS_CHECK(make_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
-    SOS_CHECK(make_map(&mA, a16_cur, p->r, p->N, p->ld16, 64, BK));
+    SOS_CHECK(make_bf16_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
+    SOS_CHECK(make_bf16_map(&mA, a16_cur, p->r, p->N, p->ld16, 64, BK));
     UpdateEpilogue epi;
     epi.rows = (int)p->N;
     epi.cols = (int)p->r;
@@ -437,24 +321,20 @@ int launch_tc_adjoint_update(const sos_plan_s* p, const void* h16, const void* a
 
 // ---- diagnostic entry point: a plain tcgen05 BF16 GEMM ------------------------------
 
-extern "C" int sos_diag_gemm_bf16(int b_mn_major, const void* X, const void* Y, float* D, int64_t m,
-                                  int64_t n, int64_t k, int64_t ldx, int64_t ldy, int32_t* status,
-                                  void* stream) {
+extern "C" int sos_diag_gemm_bf16(int mode, const void* X, const void* Y, float* D, int64_t m, int64_t n, int64_t k,
+                                  int64_t ldx, int64_t ldy, int32_t* status, void* stream) {
     using namespace sos;
     using namespace sos::tc;
     if (!X || !Y || !D || !status || m < 1 || n < 1 || k < 1 || m > INT32_MAX || n > INT32_MAX ||
-        k > INT32_MAX)
+        k > INT32_MAX || (mode & ~3))
         return fail(SOS_E_INVALID, "sos_diag_gemm_bf16: bad argument");
+    const int b_mn_major = mode & 1;
+    const bool pairs = (mode & 2) != 0;
     int dev = 0, sms = 0;
     SOS_CUDA(cudaGetDevice(&dev));
     SOS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CUtensorMap mA, mB;
-    SOS_CHECK(make_map(&mA, X, k, m, ldx, BK, BM));
-    if (b_mn_major)
-        SOS_CHECK(make_map(&mB, Y, n, k, ldy, 64, BK));
-    else
-        SOS_CHECK(make_map(&mB, Y, k, n, ldy, BK, BN));
-    const int TI = (int)ceil_div(m, BM), TJ = (int)ceil_div(n, BN);
+    const int tm = pairs ? 256 : BM;
+    const int TI = (int)ceil_div(m, tm), TJ = (int)ceil_div(n, BN);
     std::vector<int2> tiles;
     for (int i = 0; i < TI; ++i)
         for (int j = 0; j < TJ; ++j) tiles.push_back(make_int2(i, j));
@@ -464,17 +344,24 @@ extern "C" int sos_diag_gemm_bf16(int b_mn_major, const void* X, const void* Y, 
     int rc = SOS_OK;
     cudaError_t e = cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "sos_diag_gemm_bf16: copy tiles");
-    DiagEpilogue epi;
-    epi.rows = (int)m;
-    epi.cols = (int)n;
-    epi.ld = n;
-    epi.scale = 1.0f;
-    epi.out = D;
-    if (rc == SOS_OK) {
-        rc = b_mn_major ? launch_gemm<true>(mA, mB, (int)ceil_div(k, BK), d_tiles, (int)tiles.size(), sms, epi,
-                                            status, st)
-                        : launch_gemm<false>(mA, mB, (int)ceil_div(k, BK), d_tiles, (int)tiles.size(), sms, epi,
-                                             status, st);
+    if (rc == SOS_OK && pairs) {
+        rc = diag_gemm_pair(b_mn_major, X, Y, D, m, n, k, ldx, ldy, d_tiles, (int)tiles.size(), status, st);
+    } else if (rc == SOS_OK) {
+        CUtensorMap mA, mB;
+        rc = make_bf16_map(&mA, X, k, m, ldx, BK, BM);
+        if (rc == SOS_OK)
+            rc = b_mn_major ? make_bf16_map(&mB, Y, n, k, ldy, 64, BK) : make_bf16_map(&mB, Y, k, n, ldy, BK, BN);
+        DiagEpilogue epi;
+        epi.rows = (int)m;
+        epi.cols = (int)n;
+        epi.ld = n;
+        epi.scale = 1.0f;
+        epi.out = D;
+        if (rc == SOS_OK)
+            rc = b_mn_major ? launch_gemm<true>(mA, mB, (int)ceil_div(k, BK), d_tiles, (int)tiles.size(), sms, epi,
+                                                status, st)
+                            : launch_gemm<false>(mA, mB, (int)ceil_div(k, BK), d_tiles, (int)tiles.size(), sms, epi,
+                                                 status, st);
     }
     e = cudaStreamSynchronize(st);
     if (rc == SOS_OK && e != cudaSuccess) rc = cuda_fail(e, "sos_diag_gemm_bf16: run");

@@ -1,0 +1,344 @@
+// Tensor-core kernels on CTA pairs (tcgen05.mma.cta_group::2).
+//
+// Same contractions and epilogues as kernels_tc.cu, but two CTAs on two SMs
+// compute one 256 x 256 tile together: each CTA stages its own 128 rows of the
+// A operand and half (128 rows or columns) of the B operand, the leader CTA
+// issues M = 256, N = 256, K = 16 MMAs that read both CTAs' shared memory and
+// write 128 accumulator lanes in each CTA's TMEM.  Per CTA that halves the B
+// traffic: 32 KB per 64-deep K-block instead of 48 KB, so six stages fit where
+// four did, and each SM's shared memory serves 8 KB per MMA instead of 12 KB.
+//
+//   warp 0, one lane (both CTAs) : TMA producer; completion is counted on the
+//                                  leader's mbarrier
+//   warp 1, one lane (leader)    : MMA issuer; commits are multicast to both CTAs
+//   warps 2-5 (both CTAs)        : epilogue on the CTA's own 128 rows; each warp
+//                                  signals the leader when its TMEM buffer is free
+// Every mbarrier wait is bounded by the global timer; a role that gives up sets
+// the status word and unwinds, and both CTAs still meet at the final cluster
+// barrier before TMEM is released.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "internal.h"
+#include "tc_epilogues.cuh"
+#include "tc_ptx.cuh"
+
+namespace sos {
+namespace tc2 {
+
+using namespace tc;
+
+constexpr int BM = 128;          // rows per CTA; the pair covers 256
+constexpr int PAIR_M = 256;
+constexpr int BN = 256;          // columns of the pair tile; each CTA stages 128
+constexpr int BK = 64;
+constexpr int STAGES = 6;
+constexpr int A_BYTES = BM * BK * 2;              // 16 KB
+constexpr int B_BYTES = (BN / 2) * BK * 2;        // 16 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 32 KB per CTA
+constexpr int BAR_BYTES = 256;
+constexpr int EPI_STAGE_BYTES = 4 * 32 * 33 * 4;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EPI_STAGE_BYTES;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+template <bool B_MN_MAJOR, class Epilogue>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int nkb,
+                    const int2* __restrict__ tiles, int num_tiles, Epilogue epi, int32_t* __restrict__ status) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t* base = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+    uint8_t* sA = base;
+    uint8_t* sB = base + STAGES * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile uint32_t* err = tmem_slot + 1;
+    float* epi_stage = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + BAR_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    const int pair = blockIdx.x >> 1, num_pairs = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);     // 4 epilogue warps in each CTA
+        }
+        mbar_init(drain, 1);
+        *err = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc_pair(tmem_slot, TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync_all();                   // barriers initialised and TMEM allocated in both CTAs
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+        int s = 0;
+        uint32_t ph = 0;
+        int64_t issued = 0;
+        bool ok = true;
+        for (int t = pair; t < num_tiles && ok; t += num_pairs) {
+            const int2 tile = tiles[t];
+            const int arow = tile.x * PAIR_M + (int)rank * BM;
+            const int bcol = tile.y * BN + (int)rank * (BN / 2);
+            for (int kb = 0; kb < nkb; ++kb) {
+                if (*err || !mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT_NS)) {
+                    ok = false;
+                    break;
+                }
+                if (leader) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
+                const uint32_t bar = mapa_shared(smem_u32(&full[s]), 0);
+                tma_load_2d_pair(sA + s * A_BYTES, &mapA, bar, kb * BK, arow);
+                if (B_MN_MAJOR) {
+#pragma unroll
+                    for (int j = 0; j < BN / 2 / 64; ++j)
+                        tma_load_2d_pair(sB + s * B_BYTES + j * (64 * BK * 2), &mapB, bar, bcol + 64 * j, kb * BK);
+                } else {
+                    tma_load_2d_pair(sB + s * B_BYTES, &mapB, bar, kb * BK, bcol);
+                }
+                ++issued;
+                if (++s == STAGES) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        if (!ok) {
+            *err = 1;
+            atomicCAS(status, 0, SOS_E_TIMEOUT);
+        }
+        // The leader's full barriers count both CTAs' copies: let them land.
+        if (leader)
+            for (int64_t i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
+                mbar_wait(&full[i % STAGES], (uint32_t)((i / STAGES) & 1), WAIT_LIMIT_NS);
+    } else if (warp == 1 && lane == 0 && leader) {
+        // ---------------- MMA issuer (leader) ----------------
+        constexpr uint32_t idesc = idesc_bf16_f32(PAIR_M, BN, 0, B_MN_MAJOR ? 1 : 0);
+        int s = 0;
+        uint32_t ph = 0;
+        int it = 0;
+        bool ok = true;
+        for (int t = pair; t < num_tiles && ok; t += num_pairs, ++it) {
+            const int buf = it & 1;
+            const uint32_t tph = (uint32_t)(it >> 1) & 1u;
+            if (*err || !mbar_wait(&tempty[buf], tph ^ 1u, WAIT_LIMIT_NS)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
+            for (int kb = 0; kb < nkb; ++kb) {
+                if (*err || !mbar_wait(&full[s], ph, WAIT_LIMIT_NS)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_addr = smem_u32(sA + s * A_BYTES);
+                const uint32_t b_addr = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint64_t ad = smem_desc_sw128(a_addr + kk * 32, 16, 1024);
+                    const uint64_t bd = B_MN_MAJOR ? smem_desc_sw128(b_addr + kk * 16 * 128, 64 * BK * 2, 1024)
+                                                   : smem_desc_sw128(b_addr + kk * 32, 16, 1024);
+                    umma_bf16_pair(dtm, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                }
+                umma_commit_pair_multicast(&empty[s], 0x3);
+                if (++s == STAGES) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            umma_commit_pair_multicast(&tfull[buf], 0x3);
+        }
+        if (!ok) {
+            *err = 1;
+            atomicCAS(status, 0, SOS_E_TIMEOUT);
+        }
+        umma_commit_pair_multicast(drain, 0x1);
+        mbar_wait(drain, 0, WAIT_LIMIT_NS);
+    } else if (warp >= 2) {
+        // ---------------- epilogue (both CTAs) ----------------
+        const int q = warp & 3;
+        const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), 0);
+        int it = 0;
+        for (int t = pair; t < num_tiles; t += num_pairs, ++it) {
+            const int buf = it & 1;
+            const uint32_t tph = (uint32_t)(it >> 1) & 1u;
+            const bool ready = (*err == 0) && mbar_wait(&tfull[buf], tph, WAIT_LIMIT_NS);
+            if (!__all_sync(0xffffffffu, ready)) {
+                if (lane == 0) {
+                    *err = 1;
+                    atomicCAS(status, 0, SOS_E_TIMEOUT);
+                }
+                break;
+            }
+            tc_fence_after();
+            const int2 tile = tiles[t];
+            float* stage = epi_stage + (warp - 2) * 32 * STAGE_LD;
+            const int row0 = tile.x * PAIR_M + (int)rank * BM + q * 32;
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stage[lane * STAGE_LD + j] = __uint_as_float(v[j]);
+                __syncwarp();
+                epi(row0, tile.y * BN + ch * 32, stage, lane);
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(tempty_leader0 + (uint32_t)(buf * sizeof(uint64_t)));
+        }
+    }
+    if (*err) {
+        // give copies that may still be landing a moment before the CTAs part
+        const uint64_t t0 = global_timer_ns();
+        while (global_timer_ns() - t0 < 20000) {
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();                   // the leader's MMAs read the peer's shared memory
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, TMEM_COLS);
+    }
+}
+
+}  // namespace tc2
+
+namespace {
+
+template <bool B_MN, class Epi>
+int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
+                     const Epi& epi, int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    static int max_pairs = -1;
+    auto kern = tc_gemm_pair_kernel<B_MN, Epi>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (max_pairs < 0) {
+        SOS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        int dev = 0, sms = 0;
+        SOS_CUDA(cudaGetDevice(&dev));
+        SOS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        cfg.gridDim = dim3(sms);
+        int clusters = 0;
+        SOS_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (void*)kern, &cfg));
+        if (clusters < 1) return fail(SOS_E_UNSUPPORTED, "CTA pairs: no cluster of two fits on this GPU");
+        max_pairs = clusters;     // every pair resident at once: the tile loop assumes it
+    }
+    if (num_tiles <= 0) return SOS_OK;
+    const int pairs = num_tiles < max_pairs ? num_tiles : max_pairs;
+    cfg.gridDim = dim3(2 * pairs);
+    {
+        KernelScope ks_(Epi::kName, st);
+        SOS_CUDA(cudaLaunchKernelEx(&cfg, kern, mA, mB, nkb, tiles, num_tiles, epi, status));
+    }
+    return SOS_OK;
+}
+
+}  // namespace
+
+int launch_tc_forward_pair(const sos_plan_s* p, const void* a16, float* c, int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    CUtensorMap mA, mB;
+    SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, BK, BM));
+    SOS_CHECK(make_bf16_map(&mB, a16, p->r, p->N, p->ld16, BK, BN / 2));
+    tc::SegmentSumEpilogue epi{(int)p->N, p->dev.idx, p->ld_idx, c};
+    return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), p->dev.fwd_tiles2, p->dev.num_fwd_tiles2, epi,
+                                   status, st);
+}
+
+int launch_tc_adjoint_update_pair(const sos_plan_s* p, const void* h16, const void* a16_cur, void* a16_next,
+                                  float* A, float* m, float* v, int optimizer, int64_t t, double lr, double b1,
+                                  double b2, double eps, int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    CUtensorMap mH, mA;
+    SOS_CHECK(make_bf16_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
+    SOS_CHECK(make_bf16_map(&mA, a16_cur, p->r, p->N, p->ld16, 64, BK));
+    tc::UpdateEpilogue epi;
+    epi.rows = (int)p->N;
+    epi.cols = (int)p->r;
+    epi.optimizer = optimizer;
+    epi.lr = (float)lr;
+    epi.b1 = (float)b1;
+    epi.b2 = (float)b2;
+    epi.eps = (float)eps;
+    epi.c1 = (float)(1.0 - std::pow(b1, (double)t));
+    epi.c2 = (float)(1.0 - std::pow(b2, (double)t));
+    epi.A = A;
+    epi.m = m;
+    epi.v = v;
+    epi.a16_next = static_cast<__nv_bfloat16*>(a16_next);
+    epi.ld16 = p->ld16;
+    return launch_pair_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles2, p->dev.num_adj_tiles2, epi,
+                                  status, st);
+}
+
+int launch_tc_adjoint_pair(const sos_plan_s* p, const void* h16, const void* a16, float* grad, int32_t* status,
+                           cudaStream_t st) {
+    using namespace tc2;
+    CUtensorMap mH, mA;
+    SOS_CHECK(make_bf16_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
+    SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, 64, BK));
+    tc::StoreEpilogue epi{(int)p->N, (int)p->r, p->r, 2.0f, grad};
+    return launch_pair_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles2, p->dev.num_adj_tiles2, epi,
+                                  status, st);
+}
+
+int diag_gemm_pair(int b_mn_major, const void* X, const void* Y, float* D, int64_t m, int64_t n, int64_t k,
+                   int64_t ldx, int64_t ldy, const int2* tiles, int num_tiles, int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    CUtensorMap mA, mB;
+    SOS_CHECK(make_bf16_map(&mA, X, k, m, ldx, BK, BM));
+    if (b_mn_major)
+        SOS_CHECK(make_bf16_map(&mB, Y, n, k, ldy, 64, BK));
+    else
+        SOS_CHECK(make_bf16_map(&mB, Y, k, n, ldy, BK, BN / 2));
+    tc::DiagEpilogue epi;
+    epi.rows = (int)m;
+    epi.cols = (int)n;
+    epi.ld = n;
+    epi.scale = 1.0f;
+    epi.out = D;
+    return b_mn_major ? launch_pair_gemm<true>(mA, mB, (int)ceil_div(k, BK), tiles, num_tiles, epi, status, st)
+                      : launch_pair_gemm<false>(mA, mB, (int)ceil_div(k, BK), tiles, num_tiles, epi, status, st);
+}
+
+}  // namespace sos

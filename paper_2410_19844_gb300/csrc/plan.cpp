@@ -16,6 +16,7 @@
 // Because S_j(a + b) = S_j(a) + S_j(b), the index of a product of two
 // monomials is separable:  idx(a, b) = sum_j phi_j[S_j(a) + S_j(b)].
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -164,6 +165,8 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.idx);
         cudaFree(p->dev.fwd_tiles);
         cudaFree(p->dev.adj_tiles);
+        cudaFree(p->dev.fwd_tiles2);
+        cudaFree(p->dev.adj_tiles2);
         cudaFree(p->dev.pair_ptr);
         cudaFree(p->dev.pair_pos);
         if (cur >= 0) cudaSetDevice(cur);
@@ -221,7 +224,8 @@ namespace sos {
 // i.e. J >= floor(I / 2).  The adjoint covers N x r in tiles of 128 x 256.
 // Both lists walk bands of row blocks so that the CTAs running at the same
 // time share operand panels in L2.
-static void make_tiles(const sos_plan_s* p, std::vector<int2>& fwd, std::vector<int2>& adj) {
+static void make_tiles(const sos_plan_s* p, std::vector<int2>& fwd, std::vector<int2>& adj,
+                       std::vector<int2>& fwd2, std::vector<int2>& adj2) {
     const int TI = (int)ceil_div(p->N, 128), TJ = (int)ceil_div(p->N, 256);
     const int band = 16;
     for (int i0 = 0; i0 < TI; i0 += band) {
@@ -236,6 +240,28 @@ static void make_tiles(const sos_plan_s* p, std::vector<int2>& fwd, std::vector<
         for (int K = 0; K < TK; ++K)
             for (int I = i0; I < i1; ++I) adj.push_back(make_int2(I, K));
     }
+    // 256 x 256 tiles for CTA pairs: upper triangle J >= I, bands of 8 row blocks
+    const int TP = (int)ceil_div(p->N, 256), band2 = 8;
+    for (int i0 = 0; i0 < TP; i0 += band2) {
+        const int i1 = std::min(TP, i0 + band2);
+        for (int J = i0; J < TP; ++J)
+            for (int I = i0; I < i1; ++I)
+                if (J >= I) fwd2.push_back(make_int2(I, J));
+    }
+    for (int i0 = 0; i0 < TP; i0 += band2) {
+        const int i1 = std::min(TP, i0 + band2);
+        for (int K = 0; K < TK; ++K)
+            for (int I = i0; I < i1; ++I) adj2.push_back(make_int2(I, K));
+    }
+}
+
+bool use_cta_pairs() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("SOS_CTA_PAIRS");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
 }
 
 int ensure_device(sos_plan_s* p) {
@@ -249,13 +275,19 @@ int ensure_device(sos_plan_s* p) {
     t.device = cur;
     SOS_CUDA(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, cur));
     const size_t idx_bytes = (size_t)p->N * (size_t)p->ld_idx * sizeof(int32_t);
-    std::vector<int2> fwd, adj;
-    make_tiles(p, fwd, adj);
+    std::vector<int2> fwd, adj, fwd2, adj2;
+    make_tiles(p, fwd, adj, fwd2, adj2);
     uint8_t* d_S = nullptr;
     int32_t* d_phi = nullptr;
     cudaError_t e = cudaMalloc(&t.idx, idx_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&t.fwd_tiles, fwd.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&t.adj_tiles, adj.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&t.fwd_tiles2, fwd2.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&t.adj_tiles2, adj2.size() * sizeof(int2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.fwd_tiles2, fwd2.data(), fwd2.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.adj_tiles2, adj2.data(), adj2.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&d_S, p->Sd.size());
     if (e == cudaSuccess) e = cudaMalloc(&d_phi, p->phi.size() * sizeof(int32_t));
     if (e == cudaSuccess)
@@ -281,10 +313,14 @@ int ensure_device(sos_plan_s* p) {
         cudaFree(t.idx);
         cudaFree(t.fwd_tiles);
         cudaFree(t.adj_tiles);
+        cudaFree(t.fwd_tiles2);
+        cudaFree(t.adj_tiles2);
         return rc;
     }
     t.num_fwd_tiles = (int)fwd.size();
     t.num_adj_tiles = (int)adj.size();
+    t.num_fwd_tiles2 = (int)fwd2.size();
+    t.num_adj_tiles2 = (int)adj2.size();
     p->dev = t;
     return SOS_OK;
 }

@@ -1,0 +1,145 @@
+// Epilogues of the tcgen05 GEMM cores (kernels_tc.cu, kernels_tc2.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace sos {
+
+// Tensor map of a bf16 matrix (kernels_tc.cu).
+int make_bf16_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
+                  uint32_t box_inner, uint32_t box_outer);
+int diag_gemm_pair(int b_mn_major, const void* X, const void* Y, float* D, int64_t m, int64_t n, int64_t k,
+                   int64_t ldx, int64_t ldy, const int2* tiles, int num_tiles, int32_t* status, cudaStream_t st);
+
+namespace tc {
+
+// ---- epilogues ---------------------------------------------------------------
+//
+// The epilogue warps read the accumulator 32 x 32 at a time: warp q (= warp % 4)
+// owns rows 32q .. 32q+31 of the 128-row tile, and each tcgen05.ld gives lane i
+// row 32q+i, 32 consecutive columns.  The block is transposed through padded
+// shared memory (stage[i * 33 + j] = row i, column j) so that an epilogue works
+// with lane j = column j and walks the 32 rows: every global load and store of
+// a row segment is then one coalesced 128-byte access.
+
+constexpr int STAGE_LD = 33;
+
+// Forward: c[idx(a, b)] += w G_ab for b >= a (w = 1 on the diagonal, 2 above).
+// All 32 index loads are issued before the first atomic, so they overlap.
+struct SegmentSumEpilogue {
+    static constexpr const char* kName = "tc_forward";
+    int N;
+    const int32_t* idx;
+    int64_t ld_idx;
+    float* c;
+
+    __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
+        if (a0 >= N || b0 >= N || b0 + 31 < a0) return;
+        const int b = b0 + lane;
+        if (b >= N) return;
+        const int32_t* col = idx + (int64_t)a0 * ld_idx + b;
+        int32_t g[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int a = a0 + i;
+            g[i] = (a < N && a <= b) ? __ldg(col + (int64_t)i * ld_idx) : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (g[i] >= 0) {
+                const float v = stage[i * STAGE_LD + lane];
+                atomicAdd(c + g[i], a0 + i == b ? v : 2.0f * v);
+            }
+        }
+    }
+};
+
+// Adjoint / diagnostic GEMM: out[row][col] = scale * acc.
+struct StoreEpilogue {
+    static constexpr const char* kName = "tc_adjoint";
+    int rows, cols;
+    int64_t ld;
+    float scale;
+    float* out;
+
+    __device__ __forceinline__ void operator()(int a0, int k0, const float* stage, int lane) const {
+        const int k = k0 + lane;
+        if (a0 >= rows || k >= cols) return;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const int a = a0 + i;
+            if (a >= rows) break;
+            out[(int64_t)a * ld + k] = scale * stage[i * STAGE_LD + lane];
+        }
+    }
+};
+
+struct DiagEpilogue : StoreEpilogue {
+    static constexpr const char* kName = "tc_gemm_diag";
+};
+
+// Adjoint with the optimiser step fused in: grad = 2 acc, then gradient
+// descent or Adam on the FP32 master A (and m, v), and the bf16 copy of the
+// updated A written to the other buffer of the ping-pong pair (the current one
+// is still being read as an operand by other tiles).
+struct UpdateEpilogue {
+    static constexpr const char* kName = "tc_adjoint_update";
+    int rows, cols, optimizer;
+    float lr, b1, b2, eps, c1, c2;
+    float* A;
+    float* m;
+    float* v;
+    __nv_bfloat16* a16_next;
+    int64_t ld16;
+
+    // Processes the 32 rows in two halves; each half issues all its global
+    // loads before using any of them.
+    __device__ __forceinline__ void operator()(int a0, int k0, const float* stage, int lane) const {
+        const int k = k0 + lane;
+        if (a0 >= rows || k >= cols) return;
+        const float one = 1.0f;
+        const int nrows = rows - a0 < 32 ? rows - a0 : 32;
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
+            float x[16], mm[16], vv[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int64_t e = (int64_t)(a0 + h + i) * cols + k;
+                const bool ok = h + i < nrows;
+                x[i] = ok ? A[e] : 0.0f;
+                if (optimizer != SOS_GD) {
+                    mm[i] = ok ? m[e] : 0.0f;
+                    vv[i] = ok ? v[e] : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (h + i >= nrows) break;
+                const int64_t e = (int64_t)(a0 + h + i) * cols + k;
+                const float g = 2.0f * stage[(h + i) * STAGE_LD + lane];
+                float xi = x[i];
+                if (optimizer == SOS_GD) {
+                    xi -= lr * g;
+                } else {
+                    const float mi = b1 * mm[i] + (one - b1) * g;
+                    const float vi = b2 * vv[i] + (one - b2) * g * g;
+                    m[e] = mi;
+                    v[e] = vi;
+                    const float mhat = mi / c1;
+                    const float vhat = vi / c2;
+                    xi -= lr * mhat / (sqrtf(vhat) + eps);
+                }
+                A[e] = xi;
+                a16_next[(int64_t)(a0 + h + i) * ld16 + k] = __float2bfloat16_rn(xi);
+            }
+        }
+    }
+};
+
+}  // namespace tc
+}  // namespace sos

@@ -48,9 +48,11 @@ def problem(n, two_d, r=None, seed=0, squares=5):
 
 # -- the tcgen05 GEMM core ------------------------------------------------------------
 
-@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 512, 128), (200, 300, 100), (384, 256, 1000)])
+@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (256, 512, 128), (200, 300, 100), (384, 256, 1000),
+                                   (640, 520, 320)])
 @pytest.mark.parametrize("b_mn", [0, 1])
-def test_tc_gemm_matches_fp64_matmul(m, n, k, b_mn):
+@pytest.mark.parametrize("pairs", [0, 1])
+def test_tc_gemm_matches_fp64_matmul(m, n, k, b_mn, pairs):
     g = torch.Generator().manual_seed(m * 7 + n * 3 + k + b_mn)
     X = torch.randn(m, k, generator=g).bfloat16()
     Y = torch.randn(k, n, generator=g).bfloat16() if b_mn else torch.randn(n, k, generator=g).bfloat16()
@@ -63,7 +65,7 @@ def test_tc_gemm_matches_fp64_matmul(m, n, k, b_mn):
     Yd[:, :Y.shape[1]] = Y.to(DEV)
     D = torch.full((m, n), float("nan"), dtype=torch.float32, device=DEV)
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
-    L.sos_diag_gemm_bf16(b_mn, Xd.data_ptr(), Yd.data_ptr(), D.data_ptr(), m, n, k, ldx, ldy,
+    L.sos_diag_gemm_bf16(b_mn | (2 * pairs), Xd.data_ptr(), Yd.data_ptr(), D.data_ptr(), m, n, k, ldx, ldy,
                          status.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert int(status.item()) == 0
     got = D.double().cpu().numpy()
