@@ -153,7 +153,14 @@ typedef struct {
     int optimizer;      /* sos_opt */
     double lr;
     double beta1, beta2, eps;
+    int flags;          /* 0, or SOS_STEP_FP32_ADJOINT */
 } sos_step_opts;
+
+/* With SOS_FP64: contract the adjoint 2 H(r) A in FP32 from the FP64
+ * residual and iterate (the forward, residual, loss and update stay FP64).
+ * The gradient is then accurate to FP32 relative to its own size, which is
+ * all a descent step needs, and the step costs a third of the FP64 work. */
+#define SOS_STEP_FP32_ADJOINT 1
 
 /* Optimiser state, all dev, caller-owned: A (N x r) updated in place; m and
  * v (N x r, zero before the first Adam step; unused by GD); t = number of
@@ -211,6 +218,7 @@ typedef struct {
     int64_t stall_checks;     /* ... or after this many checks without a 1% gain;
                                  FP32 -> FP64 after as many */
     int64_t fp64_steps;       /* step budget of the FP64 stage (0: none) */
+    int fp64_fp32_adjoint;    /* FP64 stage steps with SOS_STEP_FP32_ADJOINT */
     double cert_tol;          /* certificate threshold (Sec. 3: about 1e-8) */
     int start_prec;           /* SOS_BF16 (the ladder), SOS_FP32 (no BF16
                                  stage) or SOS_FP64 (FP64 steps only) */
@@ -227,8 +235,8 @@ typedef struct {
 } sos_result;
 
 /* Defaults: Adam, lr 1e-2 in every stage, 20000 BF16+FP32 steps, checks
- * every 50, switch at 1e-3 or 4 stalled checks, 2000 FP64 steps, tolerance
- * 1e-8, start in BF16. */
+ * every 50, switch at 1e-3 or 4 stalled checks, 2000 FP64 steps with the
+ * FP32 adjoint, tolerance 1e-8, start in BF16. */
 int sos_solve_opts_default(sos_solve_opts* opts);
 
 /* Minimises 1/2 ||c(A) - p||^2 from the start point A by the precision

@@ -41,9 +41,12 @@ class SOSError(RuntimeError):
         self.code = code
 
 
+SOS_STEP_FP32_ADJOINT = 1
+
+
 class sos_step_opts(ctypes.Structure):
     _fields_ = [("optimizer", ctypes.c_int), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
-                ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("flags", ctypes.c_int)]
 
 
 class sos_state(ctypes.Structure):
@@ -56,7 +59,8 @@ class sos_solve_opts(ctypes.Structure):
                 ("lr_fp64", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("max_steps", ctypes.c_int64), ("check_every", ctypes.c_int64),
                 ("switch_rel", ctypes.c_double), ("stall_checks", ctypes.c_int64),
-                ("fp64_steps", ctypes.c_int64), ("cert_tol", ctypes.c_double), ("start_prec", ctypes.c_int)]
+                ("fp64_steps", ctypes.c_int64), ("fp64_fp32_adjoint", ctypes.c_int),
+                ("cert_tol", ctypes.c_double), ("start_prec", ctypes.c_int)]
 
 
 class sos_result(ctypes.Structure):

@@ -41,7 +41,7 @@ int forward(sos_plan_s* p, int prec, const void* A, void* ws, cudaStream_t st, v
 }
 
 int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad, void* loss, void* ws,
-              cudaStream_t st) {
+              cudaStream_t st, bool fp32_contraction = false) {
     const Workspace w = workspace_layout(p, prec);
     SOS_CHECK(forward(p, prec, A, ws, st, nullptr));
     double* L = loss ? static_cast<double*>(loss) : at<double>(ws, w.loss);
@@ -53,7 +53,7 @@ int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad
                                           partials, status, 1, st));
         if (grad)
             SOS_CHECK(launch_simt_adjoint<double>(p, static_cast<const double*>(A), resid,
-                                                  static_cast<double*>(grad), 1, st));
+                                                  static_cast<double*>(grad), 1, st, fp32_contraction));
         return SOS_OK;
     }
     float* resid = at<float>(ws, w.resid);
@@ -169,6 +169,7 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
     SOS_CHECK(check_ptr(ws, "sos_step: workspace"));
     if (o->optimizer == SOS_ADAM && (!s->m || !s->v)) return fail(SOS_E_INVALID, "sos_step: Adam needs m and v");
     if (o->optimizer != SOS_ADAM && o->optimizer != SOS_GD) return fail(SOS_E_INVALID, "sos_step: bad optimizer");
+    if (o->flags & ~SOS_STEP_FP32_ADJOINT) return fail(SOS_E_INVALID, "sos_step: unknown flags");
     SOS_CHECK(ensure_device(p));
     cudaStream_t st = (cudaStream_t)stream;
     const Workspace w = workspace_layout(p, prec);
@@ -201,7 +202,8 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         return SOS_OK;
     }
     void* grad = at<char>(ws, w.grad);
-    SOS_CHECK(loss_grad(p, prec, s->A, pv, grad, loss, ws, st));
+    SOS_CHECK(loss_grad(p, prec, s->A, pv, grad, loss, ws, st,
+                        prec == SOS_FP64 && (o->flags & SOS_STEP_FP32_ADJOINT)));
     if (prec == SOS_FP64)
         SOS_CHECK(launch_update<double>(p->N, p->r, static_cast<double*>(s->A), static_cast<double*>(s->m),
                                         static_cast<double*>(s->v), static_cast<const double*>(grad), o->optimizer,

@@ -120,7 +120,7 @@ int launch_residual(const sos_plan_s* plan, const T* c, const T* p, T* resid, do
                     double* partials, int32_t* status, int64_t batch, cudaStream_t st);
 template <typename T>
 int launch_simt_adjoint(const sos_plan_s* plan, const T* A, const T* resid, T* grad,
-                        int64_t batch, cudaStream_t st);
+                        int64_t batch, cudaStream_t st, bool fp32_contraction = false);
 int launch_build_h16(const sos_plan_s* plan, const float* resid, void* h16, cudaStream_t st);
 template <typename T>
 int launch_update(int64_t N, int64_t r, T* A, T* m, T* v, const T* grad, int optimizer,

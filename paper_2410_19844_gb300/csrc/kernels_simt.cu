@@ -244,7 +244,9 @@ residual_kernel(const T* __restrict__ c, const T* __restrict__ p, T* __restrict_
 // chunks of 16.  H[a][b] = r[idx[a][b]] is read straight from the residual
 // while staging, so H is never stored.
 
-template <typename T>
+// Tc is the arithmetic type of the contraction: T, or float for FP64 steps
+// that take their gradient in FP32 from the FP64 residual and iterate.
+template <typename T, typename Tc>
 __global__ void __launch_bounds__(kThreads)
 simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const int32_t* __restrict__ idx,
                     int64_t ld_idx, int64_t N, int64_t r, T* __restrict__ grad, int64_t strideA,
@@ -252,15 +254,15 @@ simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const 
     A += (int64_t)blockIdx.z * strideA;
     grad += (int64_t)blockIdx.z * strideA;
     resid += (int64_t)blockIdx.z * strideR;
-    __shared__ T Hs[16][64];
-    __shared__ T Bs[16][64];
+    __shared__ Tc Hs[16][64];
+    __shared__ Tc Bs[16][64];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t row0 = (int64_t)blockIdx.y * 64, col0 = (int64_t)blockIdx.x * 64;
-    T acc[4][4];
+    Tc acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int j = 0; j < 4; ++j) acc[i][j] = Tc(0);
     for (int64_t b0 = 0; b0 < N; b0 += 16) {
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
@@ -268,18 +270,18 @@ simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const 
             {   // H tile: 64 rows a x 16 columns b
                 const int rr = e >> 4, kk = e & 15;
                 const int64_t a = row0 + rr, b = b0 + kk;
-                Hs[kk][rr] = (a < N && b < N) ? resid[idx[a * ld_idx + b]] : T(0);
+                Hs[kk][rr] = (a < N && b < N) ? (Tc)resid[idx[a * ld_idx + b]] : Tc(0);
             }
             {   // A tile: 16 rows b x 64 columns k
                 const int kk = e >> 6, cc = e & 63;
                 const int64_t b = b0 + kk, k = col0 + cc;
-                Bs[kk][cc] = (b < N && k < r) ? A[b * r + k] : T(0);
+                Bs[kk][cc] = (b < N && k < r) ? (Tc)A[b * r + k] : Tc(0);
             }
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            T a[4], b[4];
+            Tc a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = Hs[kk][ty + 16 * i];
 #pragma unroll
@@ -298,7 +300,7 @@ simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t k = col0 + tx + 16 * j;
-            if (k < r) grad[a * r + k] = T(2) * acc[i][j];
+            if (k < r) grad[a * r + k] = T(2) * (T)acc[i][j];
         }
     }
 }
@@ -480,15 +482,19 @@ int launch_residual(const sos_plan_s* p, const T* c, const T* pv, T* resid, doub
 }
 
 template <typename T>
-int launch_simt_adjoint(const sos_plan_s* p, const T* A, const T* resid, T* grad, int64_t batch,
-                        cudaStream_t st) {
+int launch_simt_adjoint(const sos_plan_s* p, const T* A, const T* resid, T* grad, int64_t batch, cudaStream_t st,
+                        bool fp32_contraction) {
     const int64_t TI = ceil_div(p->N, 64), TK = ceil_div(p->r, 64);
     if (TI > 65535 || batch > 65535 || TK > INT32_MAX) return fail(SOS_E_UNSUPPORTED, "simt_adjoint: too many tiles");
     dim3 grid((unsigned)TK, (unsigned)TI, (unsigned)batch);
     {
-        KernelScope ks_("simt_adjoint", st);
-        simt_adjoint_kernel<T><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r, grad,
-                                                          p->N * p->r, p->M);
+        KernelScope ks_(fp32_contraction ? "simt_adjoint_fp32c" : "simt_adjoint", st);
+        if (fp32_contraction)
+            simt_adjoint_kernel<T, float><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r,
+                                                                     grad, p->N * p->r, p->M);
+        else
+            simt_adjoint_kernel<T, T><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r, grad,
+                                                                 p->N * p->r, p->M);
     }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
@@ -552,9 +558,9 @@ template int launch_residual<float>(const sos_plan_s*, const float*, const float
 template int launch_residual<double>(const sos_plan_s*, const double*, const double*, double*, double*,
                                      double*, int32_t*, int64_t, cudaStream_t);
 template int launch_simt_adjoint<float>(const sos_plan_s*, const float*, const float*, float*, int64_t,
-                                        cudaStream_t);
+                                        cudaStream_t, bool);
 template int launch_simt_adjoint<double>(const sos_plan_s*, const double*, const double*, double*, int64_t,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 template int launch_update<float>(int64_t, int64_t, float*, float*, float*, const float*, int, int64_t, double,
                                   double, double, double, void*, int64_t, cudaStream_t);
 template int launch_update<double>(int64_t, int64_t, double*, double*, double*, const double*, int, int64_t,

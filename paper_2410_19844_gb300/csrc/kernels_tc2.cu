@@ -5,8 +5,8 @@
 // A operand and half (128 rows or columns) of the B operand, the leader CTA
 // issues M = 256, N = 256, K = 16 MMAs that read both CTAs' shared memory and
 // write 128 accumulator lanes in each CTA's TMEM.  Per CTA that halves the B
-// traffic: 32 KB per 64-deep K-block instead of 48 KB, so six stages fit where
-// four did, and each SM's shared memory serves 8 KB per MMA instead of 12 KB.
+// traffic: 32 KB per 64-deep K-block instead of 48 KB, and each SM's shared
+// memory serves 8 KB per MMA instead of 12 KB.
 //
 //   warp 0, one lane (both CTAs) : TMA producer; completion is counted on the
 //                                  leader's mbarrier
@@ -35,10 +35,19 @@ constexpr int BM = 128;          // rows per CTA; the pair covers 256
 constexpr int PAIR_M = 256;
 constexpr int BN = 256;          // columns of the pair tile; each CTA stages 128
 constexpr int BK = 64;
-constexpr int STAGES = 6;
-constexpr int A_BYTES = BM * BK * 2;              // 16 KB
-constexpr int B_BYTES = (BN / 2) * BK * 2;        // 16 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 32 KB per CTA
+// A stage holds KATOMS consecutive 64-deep K-blocks ("atoms", one 128-byte
+// swizzle span each) of both operands and is released by one commit: a
+// tcgen05.commit costs the tensor pipe on the order of a hundred
+// nanoseconds, so committing per atom wastes a sizeable share of the
+// mainloop.  Three stages of two atoms keep the same 192 KB in flight as six
+// stages of one.
+constexpr int KATOMS = 2;
+constexpr int STAGES = 3;
+constexpr int ATOM_A = BM * BK * 2;               // 16 KB
+constexpr int ATOM_B = (BN / 2) * BK * 2;         // 16 KB
+constexpr int A_BYTES = KATOMS * ATOM_A;          // per stage
+constexpr int B_BYTES = KATOMS * ATOM_B;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 64 KB per CTA
 constexpr int BAR_BYTES = 256;
 constexpr int EPI_STAGE_BYTES = 4 * 32 * 33 * 4;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EPI_STAGE_BYTES;
@@ -103,20 +112,25 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             const int2 tile = tiles[t];
             const int arow = tile.x * PAIR_M + (int)rank * BM;
             const int bcol = tile.y * BN + (int)rank * (BN / 2);
-            for (int kb = 0; kb < nkb; ++kb) {
+            for (int kb = 0; kb < nkb; kb += KATOMS) {
                 if (*err || !mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT_NS)) {
                     ok = false;
                     break;
                 }
                 if (leader) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
                 const uint32_t bar = mapa_shared(smem_u32(&full[s]), 0);
-                tma_load_2d_pair(sA + s * A_BYTES, &mapA, bar, kb * BK, arow);
-                if (B_MN_MAJOR) {
 #pragma unroll
-                    for (int j = 0; j < BN / 2 / 64; ++j)
-                        tma_load_2d_pair(sB + s * B_BYTES + j * (64 * BK * 2), &mapB, bar, bcol + 64 * j, kb * BK);
-                } else {
-                    tma_load_2d_pair(sB + s * B_BYTES, &mapB, bar, kb * BK, bcol);
+                for (int at = 0; at < KATOMS; ++at) {
+                    const int kx = (kb + at) * BK;      // beyond K: zero fill, still counted
+                    tma_load_2d_pair(sA + s * A_BYTES + at * ATOM_A, &mapA, bar, kx, arow);
+                    if (B_MN_MAJOR) {
+#pragma unroll
+                        for (int j = 0; j < BN / 2 / 64; ++j)
+                            tma_load_2d_pair(sB + s * B_BYTES + at * ATOM_B + j * (64 * BK * 2), &mapB, bar,
+                                             bcol + 64 * j, kx);
+                    } else {
+                        tma_load_2d_pair(sB + s * B_BYTES + at * ATOM_B, &mapB, bar, kx, bcol);
+                    }
                 }
                 ++issued;
                 if (++s == STAGES) {
@@ -149,7 +163,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             }
             tc_fence_after();
             const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
-            for (int kb = 0; kb < nkb; ++kb) {
+            for (int kb = 0; kb < nkb; kb += KATOMS) {
                 if (*err || !mbar_wait(&full[s], ph, WAIT_LIMIT_NS)) {
                     ok = false;
                     break;
@@ -158,11 +172,15 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 const uint32_t a_addr = smem_u32(sA + s * A_BYTES);
                 const uint32_t b_addr = smem_u32(sB + s * B_BYTES);
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    const uint64_t ad = smem_desc_sw128(a_addr + kk * 32, 16, 1024);
-                    const uint64_t bd = B_MN_MAJOR ? smem_desc_sw128(b_addr + kk * 16 * 128, 64 * BK * 2, 1024)
-                                                   : smem_desc_sw128(b_addr + kk * 32, 16, 1024);
-                    umma_bf16_pair(dtm, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                for (int at = 0; at < KATOMS; ++at) {
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t ad = smem_desc_sw128(a_addr + at * ATOM_A + kk * 32, 16, 1024);
+                        const uint64_t bd =
+                            B_MN_MAJOR ? smem_desc_sw128(b_addr + at * ATOM_B + kk * 16 * 128, 64 * BK * 2, 1024)
+                                       : smem_desc_sw128(b_addr + at * ATOM_B + kk * 32, 16, 1024);
+                        umma_bf16_pair(dtm, ad, bd, idesc, (kb | at | kk) != 0 ? 1u : 0u);
+                    }
                 }
                 umma_commit_pair_multicast(&empty[s], 0x3);
                 if (++s == STAGES) {

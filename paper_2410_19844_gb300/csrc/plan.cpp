@@ -240,16 +240,25 @@ static void make_tiles(const sos_plan_s* p, std::vector<int2>& fwd, std::vector<
         for (int K = 0; K < TK; ++K)
             for (int I = i0; I < i1; ++I) adj.push_back(make_int2(I, K));
     }
-    // 256 x 256 tiles for CTA pairs: upper triangle J >= I, bands of 8 row blocks
-    const int TP = (int)ceil_div(p->N, 256), band2 = 8;
-    for (int i0 = 0; i0 < TP; i0 += band2) {
-        const int i1 = std::min(TP, i0 + band2);
+    // 256 x 256 tiles for CTA pairs: upper triangle J >= I for the forward.
+    // Both lists walk bands of row blocks (rows fastest inside a band) so the
+    // pairs running at once share operand panels in L2; the band heights can
+    // be overridden with SOS_BAND_FWD / SOS_BAND_ADJ (tuning).
+    const int TP = (int)ceil_div(p->N, 256);
+    auto env_band = [](const char* name, int dflt) {
+        const char* e = std::getenv(name);
+        const int v = e ? std::atoi(e) : 0;
+        return v > 0 ? v : dflt;
+    };
+    const int bf = env_band("SOS_BAND_FWD", 8), ba = env_band("SOS_BAND_ADJ", 8);
+    for (int i0 = 0; i0 < TP; i0 += bf) {
+        const int i1 = std::min(TP, i0 + bf);
         for (int J = i0; J < TP; ++J)
             for (int I = i0; I < i1; ++I)
                 if (J >= I) fwd2.push_back(make_int2(I, J));
     }
-    for (int i0 = 0; i0 < TP; i0 += band2) {
-        const int i1 = std::min(TP, i0 + band2);
+    for (int i0 = 0; i0 < TP; i0 += ba) {
+        const int i1 = std::min(TP, i0 + ba);
         for (int K = 0; K < TK; ++K)
             for (int I = i0; I < i1; ++I) adj2.push_back(make_int2(I, K));
     }

@@ -58,6 +58,7 @@ int sos_solve_opts_default(sos_solve_opts* o) {
     o->switch_rel = 1e-3;
     o->stall_checks = 4;
     o->fp64_steps = 2000;
+    o->fp64_fp32_adjoint = 1;
     o->cert_tol = 1e-8;
     o->start_prec = SOS_BF16;
     return SOS_OK;
@@ -148,7 +149,7 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
             }
             if (prec == SOS_FP32 && (stall >= o->stall_checks || rel <= 0.25 * o->cert_tol)) break;
         }
-        sos_step_opts so{o->optimizer, prec == SOS_BF16 ? o->lr_bf16 : o->lr_fp32, o->beta1, o->beta2, o->eps};
+        sos_step_opts so{o->optimizer, prec == SOS_BF16 ? o->lr_bf16 : o->lr_fp32, o->beta1, o->beta2, o->eps, 0};
         SOS_CHECK(sos_step(p, prec, &s, p32, &so, nullptr, prec == SOS_BF16 ? ws16 : ws32, stream));
         ++step;
     }
@@ -183,7 +184,8 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
                 }
                 if (rel <= 0.5 * o->cert_tol || k == o->fp64_steps) break;
             }
-            sos_step_opts so{o->optimizer, o->lr_fp64, o->beta1, o->beta2, o->eps};
+            sos_step_opts so{o->optimizer, o->lr_fp64, o->beta1, o->beta2, o->eps,
+                             o->fp64_fp32_adjoint ? SOS_STEP_FP32_ADJOINT : 0};
             SOS_CHECK(sos_step(p, SOS_FP64, &s64, p64, &so, nullptr, ws64, stream));
             ++out->steps_fp64;
         }

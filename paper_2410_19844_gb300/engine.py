@@ -144,12 +144,12 @@ class Optimizer:
     through sos_step."""
 
     def __init__(self, plan: Plan, A: torch.Tensor, prec="bf16", optimizer="adam", lr=1e-2,
-                 beta1=0.9, beta2=0.999, eps=1e-8):
+                 beta1=0.9, beta2=0.999, eps=1e-8, fp32_adjoint=False):
         self.plan, self.prec = plan, _prec(prec)
         plan._check(A, self.prec)
         self.A = A
         self.opts = L.sos_step_opts(L.SOS_ADAM if optimizer == "adam" else L.SOS_GD, lr, beta1,
-                                    beta2, eps)
+                                    beta2, eps, L.SOS_STEP_FP32_ADJOINT if fp32_adjoint else 0)
         if optimizer == "adam":
             self.m, self.v = torch.zeros_like(A), torch.zeros_like(A)
         else:

@@ -295,3 +295,18 @@ def test_step_fp32_matches_oracle(optimizer):
         if optimizer == "adam":
             m = opt.m.double().cpu().numpy().copy()
             v = opt.v.double().cpu().numpy().copy()
+
+
+def test_fp64_step_with_fp32_adjoint():
+    """FP64 iterate, residual and update; the adjoint contracted in FP32: the
+    gradient a GD step applies is the oracle's to FP32 accuracy."""
+    o, A, p = problem(6, 8, 210)
+    pl = Plan(6, 8, 210)
+    A_dev = torch.from_numpy(A.copy()).to(DEV)
+    lr = 1e-3
+    opt = Optimizer(pl, A_dev, prec="fp64", optimizer="gd", lr=lr, fp32_adjoint=True)
+    loss = opt.step(torch.from_numpy(p).to(DEV))[0].item()
+    loss_ref, g_ref, _ = o.loss_grad(A, p)
+    assert abs(loss - loss_ref) <= 1e-12 * loss_ref          # the forward is still FP64
+    g_applied = (A - A_dev.cpu().numpy()) / lr
+    assert rel(g_applied, g_ref) < 1e-5
