@@ -78,7 +78,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree build, or the file named by SOS_LIBRARY_PATH (another build
+    of the same sources, e.g. with different tile constants)."""
+    return os.environ.get("SOS_LIBRARY_PATH") or _build.LIB
 
 
 def lib(auto_build: bool = True):
@@ -86,7 +88,10 @@ def lib(auto_build: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if auto_build else _build.LIB
+    if os.environ.get("SOS_LIBRARY_PATH"):
+        path = os.environ["SOS_LIBRARY_PATH"]
+    else:
+        path = _build.build() if auto_build else _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library missing at {path}; run __graft_entry__.build()")
     L = ctypes.CDLL(path)
