@@ -126,6 +126,15 @@ class ClockSampler:
 
 # -- traffic figures committed from ncu -------------------------------------------------
 
+def sources_sha(paths) -> str:
+    """First 16 hex digits of the SHA-256 over the listed files (repo-relative)."""
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def committed_traffic(kernel: str):
     """dram bytes per launch from profiles/traffic.json, or None when the kernel
     source changed since the capture."""
@@ -133,9 +142,7 @@ def committed_traffic(kernel: str):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         rec = d[kernel]
-        src = os.path.join(ROOT, rec["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return rec["bytes_per_launch"] if sha == rec["source_sha"] else None
+        return rec["bytes_per_launch"] if sources_sha(rec["sources"]) == rec["sources_sha"] else None
     except Exception:
         return None
 

@@ -329,6 +329,13 @@ int sos_diag_gemm_bf16(int mode, const void* X, const void* Y, float* D,
                        int64_t m, int64_t n, int64_t k, int64_t ldx, int64_t ldy,
                        int32_t* status, void* stream);
 
+/* Diagnostic for failure detection: one device thread waits, with the same
+ * bounded mbarrier wait as the tensor-core kernels, on a barrier that nothing
+ * arrives at.  After limit_ns (at most 5 s) it sets *status (dev int32, zero
+ * on entry) to SOS_E_TIMEOUT and the kernel returns; the context stays usable.
+ * Asynchronous on `stream`. */
+int sos_diag_bounded_wait(uint64_t limit_ns, int32_t* status, void* stream);
+
 /* ---- instrumentation ------------------------------------------------------ */
 
 /* Number of kernels this library has launched since it was loaded. */

@@ -70,6 +70,8 @@ def _load():
     lib.oracle_coeff_at.restype = dbl
     lib.oracle_grad_row.argtypes = [i32, vp, i64, vp, i64, i64, vp, vp, i64, vp]
     lib.oracle_grad_row.restype = i32
+    lib.oracle_resid_row.argtypes = [i32, vp, i64, vp, i64, i64, vp, vp, i64, vp]
+    lib.oracle_resid_row.restype = i32
     lib.oracle_gd_step.argtypes = [i64, dbl, vp, vp]
     lib.oracle_gd_step.restype = None
     lib.oracle_adam_step.argtypes = [i64, i64, dbl, dbl, dbl, dbl, vp, vp, vp, vp]
@@ -188,6 +190,17 @@ class Oracle:
                                      self.M, A.shape[1], _ptr(A), _ptr(p), a, _ptr(row))
         assert rc == 0
         return row
+
+    def resid_row(self, A, p, a: int) -> np.ndarray:
+        """h_b = (c(A) - p)_{a+b} for every b: row a of the matrix whose
+        contraction with A gives half the gradient."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        h = np.empty(self.N, dtype=np.float64)
+        rc = _load().oracle_resid_row(self.n, _ptr(self.Ed), self.N, _ptr(self.E2d),
+                                      self.M, A.shape[1], _ptr(A), _ptr(p), a, _ptr(h))
+        assert rc == 0
+        return h
 
     # -- optimiser (Sec. 3: "basic ADAM") ------------------------------
     @staticmethod

@@ -225,13 +225,11 @@ double oracle_coeff_at(int n, const uint8_t* Ed, int64_t N, int64_t r,
     return c;
 }
 
-/* One row a of the gradient computed on its own (for samples of problems too
- * large for the full product table):  grad_{a,k} = 2 sum_b (c - p)_{a+b} A_{b,k},
- * where every needed c_{a+b} comes from oracle_coeff_at. */
-int oracle_grad_row(int n, const uint8_t* Ed, int64_t N, const uint8_t* E2d, int64_t M,
-                    int64_t r, const double* A, const double* p, int64_t a, double* row) {
-    double* h = (double*)malloc((size_t)N * sizeof(double));
-    if (!h) return -1;
+/* Row a of the residual Hankel-like matrix, computed on its own (for samples
+ * of problems too large for the full product table):  h_b = (c - p)_{a+b}
+ * for every degree-<=d monomial b, each c_{a+b} from oracle_coeff_at. */
+int oracle_resid_row(int n, const uint8_t* Ed, int64_t N, const uint8_t* E2d, int64_t M,
+                     int64_t r, const double* A, const double* p, int64_t a, double* h) {
     int bad = 0;
     #pragma omp parallel for schedule(dynamic, 8) reduction(+:bad)
     for (int64_t b = 0; b < N; ++b) {
@@ -241,13 +239,23 @@ int oracle_grad_row(int n, const uint8_t* Ed, int64_t N, const uint8_t* E2d, int
         if (g < 0) { bad++; h[b] = 0.0; continue; }
         h[b] = oracle_coeff_at(n, Ed, N, r, A, sum) - p[g];
     }
+    return bad ? -1 : 0;
+}
+
+/* One row a of the gradient (derived from Eq. 2):
+ *   grad_{a,k} = 2 sum_b (c - p)_{a+b} A_{b,k}. */
+int oracle_grad_row(int n, const uint8_t* Ed, int64_t N, const uint8_t* E2d, int64_t M,
+                    int64_t r, const double* A, const double* p, int64_t a, double* row) {
+    double* h = (double*)malloc((size_t)N * sizeof(double));
+    if (!h) return -1;
+    int rc = oracle_resid_row(n, Ed, N, E2d, M, r, A, p, a, h);
     for (int64_t k = 0; k < r; ++k) row[k] = 0.0;
     for (int64_t b = 0; b < N; ++b) {
         const double* Ab = A + b * r;
         for (int64_t k = 0; k < r; ++k) row[k] += 2.0 * h[b] * Ab[k];
     }
     free(h);
-    return bad ? -1 : 0;
+    return rc;
 }
 
 /* Plain gradient descent: A <- A - lr * grad. */

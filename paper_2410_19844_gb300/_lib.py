@@ -31,7 +31,7 @@ EXPORTS = [
     "sos_timing_reset", "sos_timing_report", "sos_loss_from_coeffs_static", "sos_solve_opts_default",
     "sos_solve", "sos_group_create", "sos_group_destroy", "sos_group_scratch_size", "sos_group_set",
     "sos_group_clear", "sos_group_sync", "sos_group_run", "sos_group_losses", "sos_group_state",
-    "sos_convert", "sos_group_set_lr", "sos_last_error",
+    "sos_convert", "sos_group_set_lr", "sos_diag_bounded_wait", "sos_last_error",
 ]
 
 
@@ -127,6 +127,7 @@ def lib(auto_build: bool = True):
         "sos_group_losses": [vp, vp, vp],
         "sos_group_state": [vp, i32, P(vp), P(vp), P(i64)],
         "sos_convert": [vp, i32, vp, i32, i64, vp],
+        "sos_diag_bounded_wait": [ctypes.c_uint64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -321,3 +322,7 @@ def sos_convert(x, x_prec, y, y_prec, count, stream) -> None:
 
 def sos_group_set_lr(group, slot, lr) -> None:
     _check(lib().sos_group_set_lr(group, slot, lr))
+
+
+def sos_diag_bounded_wait(limit_ns, status, stream) -> None:
+    _check(lib().sos_diag_bounded_wait(limit_ns, status, stream))

@@ -319,6 +319,38 @@ int launch_tc_adjoint_update(const sos_plan_s* p, const void* h16, const void* a
 
 }  // namespace sos
 
+// ---- diagnostic: a bounded wait that runs out ------------------------------------------
+
+namespace sos {
+namespace tc {
+
+// One thread waits, with the same bounded mbarrier wait the GEMM roles use, on
+// a barrier that nothing arrives at; when the limit passes it records
+// SOS_E_TIMEOUT and the kernel returns normally.
+__global__ void bounded_wait_kernel(uint64_t limit_ns, int32_t* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait(&bar, 0, limit_ns)) atomicCAS(status, 0, SOS_E_TIMEOUT);
+    }
+}
+
+}  // namespace tc
+}  // namespace sos
+
+extern "C" int sos_diag_bounded_wait(uint64_t limit_ns, int32_t* status, void* stream) {
+    using namespace sos;
+    if (!status || limit_ns > 5000000000ull) return fail(SOS_E_INVALID, "sos_diag_bounded_wait: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        KernelScope ks_("bounded_wait", st);
+        tc::bounded_wait_kernel<<<1, 32, 0, st>>>(limit_ns, status);
+    }
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
 // ---- diagnostic entry point: a plain tcgen05 BF16 GEMM ------------------------------
 
 extern "C" int sos_diag_gemm_bf16(int mode, const void* X, const void* Y, float* D, int64_t m, int64_t n, int64_t k,

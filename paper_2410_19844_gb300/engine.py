@@ -161,6 +161,25 @@ class Optimizer:
     def t(self) -> int:
         return self.state.t
 
+    def state_dict(self) -> dict:
+        """Everything needed to continue the iteration: A, m, v, the step count and
+        the optimiser settings (the bf16 copy of A is rebuilt on resume)."""
+        d = {"A": self.A.detach().clone(), "t": int(self.state.t), "prec": self.prec,
+             "opts": {f: getattr(self.opts, f) for f, _ in self.opts._fields_}}
+        if self.m is not None:
+            d["m"], d["v"] = self.m.detach().clone(), self.v.detach().clone()
+        return d
+
+    def load_state_dict(self, d: dict) -> None:
+        self.A.copy_(d["A"])
+        if self.m is not None:
+            self.m.copy_(d["m"])
+            self.v.copy_(d["v"])
+        for f, v in d["opts"].items():
+            setattr(self.opts, f, v)
+        self.state.t = int(d["t"])
+        self.state.flags = 0
+
     def step(self, p: torch.Tensor) -> torch.Tensor:
         """One iteration; returns the device tensor {loss before the step, ||p||^2}."""
         L.sos_step(self.plan.handle, self.prec, self.state, _ptr(p), self.opts, _ptr(self.loss),

@@ -3,7 +3,8 @@
 Each query is a target p (degree <= 2d in n variables) and a start point A0;
 the answer is a verdict: SOS (an iterate with ||c(A) - p|| <= cert_tol ||p||
 in FP64 -- the paper's accuracy criterion, Sec. 3), NOT_CONVERGED (a gradient
-method never proves the opposite), or ERROR (non-finite values).
+method never proves the opposite), ERROR (non-finite values) or TIMEOUT (the
+request's deadline passed before a verdict).
 
 Requests join a running FP32 group (library groups: every active problem's
 tiles in one set of launches, replayed as a captured CUDA graph of K steps)
@@ -40,6 +41,9 @@ class Job:
     n: int
     two_d: int
     make: Callable[[], tuple]        # () -> (p64, A0_64): float64 device tensors
+
+
+VERDICT_TIMEOUT = -2   # server-level verdict: the request's deadline passed
 
 
 @dataclass
@@ -88,6 +92,7 @@ class Policy:
     max_decays: int = 2              # ... at most this many times per stage before deciding
     max_fp32_steps: int = 8000
     max_fp64_steps: int = 3000
+    deadline_s: float = float("inf")  # arrival -> verdict budget; past it the request times out
 
 
 def _footprint(plan: Plan, elt: int) -> int:
@@ -297,6 +302,11 @@ class Server:
                     L.sos_group_set_lr(self.g64, slot, a.lr)
                 elif a.stall >= pol.stall_checks or a.steps64 >= pol.max_fp64_steps:
                     self._retire(a, L.SOS_VERDICT_NOT_CONVERGED, rel, now, out)
+            # requests still open past their deadline end here, between ticks
+            for act in (self.active32, self.active64):
+                for slot, a in list(act.items()):
+                    if now - a.job.arrival_s > pol.deadline_s:
+                        self._retire(a, VERDICT_TIMEOUT, a.best, now, out)
         torch.cuda.synchronize()
         return out
 

@@ -167,3 +167,23 @@ def test_nonfinite_request_fails_alone():
     for j in good:
         want = L.SOS_VERDICT_SOS if j.rid % 2 == 0 else L.SOS_VERDICT_NOT_CONVERGED
         assert out[j.rid].verdict == want
+
+
+def test_deadline_times_requests_out_and_frees_their_slots():
+    """A request past its deadline is answered TIMEOUT between ticks and its
+    slot and memory go back to the pool; the same server then serves the
+    same requests to their normal verdicts."""
+    from paper_2410_19844_gb300.server import VERDICT_TIMEOUT
+    jobs = _stream(6, 3, 1000.0, [(4, 4), (4, 6)])
+    srv = Server(capacity=8, steps_per_tick=32, policy=Policy(deadline_s=0.0))
+    out = srv.run(jobs)
+    assert sorted(v.rid for v in out) == sorted(j.rid for j in jobs)
+    assert all(v.verdict == VERDICT_TIMEOUT for v in out)
+    assert srv.used == 0 and not srv.active32 and not srv.active64
+    assert len(srv.free32) == len(srv.free64) == 8
+    srv.policy = Policy()
+    again = {v.rid: v for v in srv.run(jobs)}
+    srv.close()
+    for j in jobs:
+        want = L.SOS_VERDICT_SOS if j.rid % 2 == 0 else L.SOS_VERDICT_NOT_CONVERGED
+        assert again[j.rid].verdict == want

@@ -205,6 +205,15 @@ def test_grad_row_matches_full():
         np.testing.assert_allclose(o.grad_row(A, p, a), g[a], rtol=1e-11, atol=1e-11)
 
 
+def test_resid_row_is_the_residual_at_monomial_sums():
+    """h_b = (c - p) at the monomial E_a + E_b, looked up in the full residual."""
+    o, A, p = _problem(4, 6, 5)
+    _, resid = o.residual(o.coeffs(A), p)
+    for a in [0, 11, o.N - 1]:
+        want = np.array([resid[o.rank(o.Ed[a].astype(int) + o.Ed[b].astype(int))] for b in range(o.N)])
+        np.testing.assert_allclose(o.resid_row(A, p, a), want, rtol=1e-12, atol=1e-12)
+
+
 # -- optimiser ------------------------------------------------------------------
 
 def test_adam_hand_worked_steps():
