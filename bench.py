@@ -186,6 +186,48 @@ def oracle_sample(w, widths=(8, 16), reps=2, seed=0):
     return 1.0 / t_full, desc, oracle.num_threads()
 
 
+def blas_sample(w, widths=(256, 512), reps=2, seed=0):
+    """Times one GD iteration written as dense CPU tensor ops (torch fp32 matmuls
+    plus index_add / gather through the oracle's pair table; no code shared
+    with the GPU path) on column slices of A, extrapolated linearly in the
+    number of columns.  Returns (iters/s for the full workload, description,
+    threads)."""
+    import torch
+
+    import oracle
+    import sos_inputs
+    t_setup = time.time()
+    o = oracle.Oracle(w.n, w.two_d)
+    idx = torch.from_numpy(o.prod.astype("int64")).reshape(-1)
+    p = torch.from_numpy(sos_inputs.normal_matrix(w.M, 1, seed)[:, 0]).float()
+    setup_s = time.time() - t_setup
+    times = {}
+    for cols in widths:
+        A = torch.from_numpy(sos_inputs.normal_matrix(w.N, cols, seed, sigma=w.init_sigma)).float()
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            G = A @ A.T
+            c = torch.zeros(w.M).index_add_(0, idx, G.reshape(-1))
+            resid = c - p
+            _loss = 0.5 * float(torch.dot(resid, resid))
+            H = resid[idx].reshape(w.N, w.N)
+            A -= 1e-7 * (2.0 * (H @ A))
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        times[cols] = best
+    (c1, t1), (c2, t2) = sorted(times.items())
+    t2 = max(t2, t1)
+    b = (t2 - t1) / (c2 - c1)
+    a = max(t1 - b * c1, 0.0)
+    t_full = a + b * w.cols
+    desc = (f"torch CPU fp32 GD iteration (A A^T, index_add into c, gather H, 2 H A) on column slices of "
+            f"width {list(times)}, best of {reps}: {', '.join(f'{k} cols {v:.3f} s' for k, v in times.items())}; "
+            f"fit t = {a:.3f} s + {b:.5f} s/col, extrapolated to {w.cols} cols = {t_full:.1f} s/iter; "
+            f"setup (pair table) {setup_s:.1f} s not timed")
+    return 1.0 / t_full, desc, torch.get_num_threads()
+
+
 def run_reference(args):
     import sos_inputs
     rank, _, world = dist_env()
@@ -436,10 +478,12 @@ def run_ours(args):
                "steps": k2, "ms_per_step": e2e_ms / k2,
                "note": "state (A, p) copied host->device and A, loss device->host every step"}
 
-    cpu = None
+    cpu = cpu_blas = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(w)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        v, desc, cores = blas_sample(w)
+        cpu_blas = {"value": v, "unit": UNIT, "cores": cores, "kind": "torch-cpu-blas", "sample": desc}
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -450,7 +494,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
                 "config": config_of(w, world), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-                "roofline": roof, "cpu_baseline": cpu, "serving": serving,
+                "roofline": roof, "cpu_baseline": cpu, "cpu_blas": cpu_blas, "serving": serving,
                 "step": {"alg_tflops": step_tflops,
                          "frac_of_sustained": step_tflops / peaks["bf16_tflops_sustained"],
                          "frac_of_burst": step_tflops / peaks["bf16_tflops"],

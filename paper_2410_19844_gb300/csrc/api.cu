@@ -99,6 +99,7 @@ int sos_workspace_init(sos_plan_t p, int prec, void* ws, void* stream) {
 }
 
 int sos_coeffs(sos_plan_t p, int prec, const void* A, void* c, void* ws, void* stream) {
+    TraceRange trace_("sos_coeffs");
     if (!p || bad_prec(prec)) return fail(SOS_E_INVALID, "sos_coeffs: bad plan or precision");
     SOS_CHECK(check_ptr(A, "sos_coeffs: A"));
     SOS_CHECK(check_ptr(c, "sos_coeffs: c"));
@@ -109,6 +110,7 @@ int sos_coeffs(sos_plan_t p, int prec, const void* A, void* c, void* ws, void* s
 
 int sos_loss_grad(sos_plan_t p, int prec, const void* A, const void* pv, void* grad, void* loss, void* ws,
                   void* stream) {
+    TraceRange trace_("sos_loss_grad");
     if (!p || bad_prec(prec)) return fail(SOS_E_INVALID, "sos_loss_grad: bad plan or precision");
     SOS_CHECK(check_ptr(A, "sos_loss_grad: A"));
     SOS_CHECK(check_ptr(pv, "sos_loss_grad: p"));
@@ -126,6 +128,7 @@ int sos_workspace_size_batched(sos_plan_t p, int prec, int64_t batch, size_t* by
 
 int sos_loss_grad_batched(sos_plan_t p, int prec, int64_t batch, const void* A, const void* pv, void* grad,
                           void* loss, void* ws, void* stream) {
+    TraceRange trace_("sos_loss_grad_batched");
     if (!p || batch < 1 || (prec != SOS_FP32 && prec != SOS_FP64))
         return fail(SOS_E_INVALID, "sos_loss_grad_batched: FP32 or FP64 and batch >= 1");
     SOS_CHECK(check_ptr(A, "sos_loss_grad_batched: A"));
@@ -163,6 +166,7 @@ int sos_loss_grad_batched(sos_plan_t p, int prec, int64_t batch, const void* A, 
 
 int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_step_opts* o, void* loss, void* ws,
              void* stream) {
+    TraceRange trace_("sos_step");
     if (!p || bad_prec(prec) || !s || !o) return fail(SOS_E_INVALID, "sos_step: bad argument");
     SOS_CHECK(check_ptr(s->A, "sos_step: state A"));
     SOS_CHECK(check_ptr(pv, "sos_step: p"));
@@ -247,6 +251,7 @@ int sos_read_status(sos_plan_t p, int prec, void* ws, void* stream) {
 
 int sos_certify(sos_plan_t p, const void* A, int a_is_double, const double* pv, double tol_rel, double* rel_out,
                 int* verdict_out, void* ws_unused, void* stream) {
+    TraceRange trace_("sos_certify");
     (void)ws_unused;
     if (!p || !A || !pv || !rel_out || !verdict_out) return fail(SOS_E_INVALID, "sos_certify: bad argument");
     SOS_CHECK(ensure_device(p));

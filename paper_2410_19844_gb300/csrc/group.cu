@@ -527,6 +527,7 @@ int sos_group_state(sos_group_t g, int slot, void** A_current, void** A_previous
 }
 
 int sos_group_sync(sos_group_t g, void* stream) {
+    TraceRange trace_("sos_group_sync");
     if (!g) return fail(SOS_E_INVALID, "sos_group_sync: NULL group");
     if (!g->dirty) return SOS_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -580,6 +581,7 @@ int sos_group_sync(sos_group_t g, void* stream) {
 // captured on the group's private stream the first time and replayed after,
 // ordered after and before the caller's stream with events.
 int sos_group_run(sos_group_t g, int steps, void* stream) {
+    TraceRange trace_("sos_group_run");
     if (!g || steps < 1 || steps > 100000) return fail(SOS_E_INVALID, "sos_group_run: bad argument");
     if (g->dirty) return fail(SOS_E_INVALID, "sos_group_run: call sos_group_sync after changing slots");
     cudaStream_t st = (cudaStream_t)stream;

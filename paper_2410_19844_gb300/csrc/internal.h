@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -43,6 +44,16 @@ class KernelScope {
     const char* name_;
     cudaStream_t st_;
     cudaEvent_t start_ = nullptr;
+};
+
+// Host-side NVTX range over an API call: shows up under Nsight tools, and
+// costs one pointer test when no tool is attached.
+class TraceRange {
+   public:
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
 };
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

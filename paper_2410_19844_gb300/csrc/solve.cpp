@@ -65,6 +65,7 @@ int sos_solve_opts_default(sos_solve_opts* o) {
 }
 
 int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* o, sos_result* out, void* stream) {
+    TraceRange trace_("sos_solve");
     if (!p || !p64 || !A || !o || !out) return fail(SOS_E_INVALID, "sos_solve: NULL argument");
     if (o->start_prec != SOS_BF16 && o->start_prec != SOS_FP32 && o->start_prec != SOS_FP64)
         return fail(SOS_E_INVALID, "sos_solve: bad start_prec");
@@ -138,6 +139,7 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
                 ++stall;
             }
             if (prec == SOS_BF16 && (rel < o->switch_rel || stall >= o->stall_checks)) {
+                nvtxMarkA("sos_solve: BF16 -> FP32");
                 out->rel_at_switch = rel;
                 out->steps_bf16 = step;
                 prec = SOS_FP32;
@@ -158,6 +160,7 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
     out->min_rel = best;
 
     // ---- FP64 stage on an FP64 copy of the best FP32 point ----
+    nvtxMarkA("sos_solve: FP64 stage");
     SOS_CHECK(mem.alloc(&A64, NR));
     SOS_CHECK(mem.alloc(&best64, NR));
     if (run32)

@@ -202,6 +202,42 @@ def test_step_fp64_matches_oracle(optimizer):
         assert rel(A_dev.cpu().numpy(), Aref) < 1e-12
 
 
+# -- degenerate shapes -------------------------------------------------------------------
+
+DEGENERATE = [(1, 2, 1),      # one variable, quadratic, one square: N = 2, M = 3
+              (1, 20, 11),    # univariate: H(r) is a true Hankel matrix
+              (1, 40, 21),
+              (2, 2, 1),      # a single square of an affine form
+              (5, 2, 1),
+              (30, 2, 6),     # many variables, degree 2: N = 31, M = 496
+              (4, 8, 1)]      # rank one at a larger degree
+
+
+@pytest.mark.parametrize("n,two_d,r", DEGENERATE)
+def test_degenerate_shapes_fp64(n, two_d, r):
+    o, A, p = problem(n, two_d, r, squares=2)
+    pl = Plan(n, two_d, r)
+    loss, _, g = pl.loss_grad(torch.from_numpy(A).to(DEV), torch.from_numpy(p).to(DEV), "fp64")
+    loss_ref, g_ref, _ = o.loss_grad(A, p)
+    assert abs(loss.item() - loss_ref) <= 1e-12 * loss_ref
+    assert rel(g.cpu().numpy(), g_ref) < 1e-12
+
+
+@pytest.mark.parametrize("n,two_d,r", DEGENERATE)
+def test_degenerate_shapes_fp32_and_bf16(n, two_d, r):
+    o, A, p = problem(n, two_d, r, squares=2)
+    pl = Plan(n, two_d, r)
+    A32 = A.astype(np.float32)
+    p32 = p.astype(np.float32).astype(np.float64)
+    loss, _, g = pl.loss_grad(torch.from_numpy(A32).to(DEV), torch.from_numpy(p32).float().to(DEV), "fp32")
+    loss_ref, g_ref, _ = o.loss_grad(A32.astype(np.float64), p32)
+    assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+    assert rel(g.cpu().numpy(), g_ref) < 1e-5
+    A16 = bf16_round(A)
+    c = pl.coeffs(torch.from_numpy(A32).to(DEV), "bf16").cpu().numpy()
+    assert rel(c, o.coeffs(A16)) < 1e-5
+
+
 # -- certificate and status ---------------------------------------------------------------
 
 def test_certify_generating_matrix():
