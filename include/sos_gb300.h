@@ -194,6 +194,66 @@ int sos_step(sos_plan_t plan, int prec, sos_state* state, const void* p,
  * (SOS_OK, SOS_E_NONFINITE or SOS_E_TIMEOUT).  Synchronises `stream`. */
 int sos_read_status(sos_plan_t plan, int prec, void* workspace, void* stream);
 
+/* ---- the network's first layer (Sec. 2, Sec. 2.1) ------------------------- */
+
+/* The paper's network produces the quartic form ||B Z A1 x||^2 in nf = n + 1
+ * variables (Sec. 2, Eq. 4; the paper calls the first-layer matrix A, here
+ * A1 to keep it apart from the coefficient matrix A):
+ *   A1  dev m x nf, row-major: the linear first layer, v = A1 x;
+ *   Z   the augmentation, (x_1 v, ..., x_nf v), index i*m + j;
+ *   B   dev k x (nf*m), row-major: k outputs, one square each.
+ * Output k is x^T M_k A1 x with M_k[i][j] = B[k][i*m + j] (B read as a stack
+ * of nf x m blocks).  With P_k = M_k A1 the form is sum_k (x^T P_k x)^2, whose
+ * coefficient matrix over the monomials x_i x_j (i <= j) is
+ *   A_hat[(i,j)][k] = P_k[i][j] + P_k[j][i] (i < j),  P_k[i][i] (i = j).
+ * The plan must have two_d = 4 and r = k; its degree-<=4 basis in n variables
+ * is the form dehomogenised (x_nf = 1), so A_hat is the plan's N x k matrix
+ * and c, the loss and its gradient are the core pass on A_hat.  The first
+ * layer does not enlarge the set of forms; Sec. 2.1 and Sec. 3.3 use it to
+ * speed up fits of targets with very unequal coefficients.
+ * Element type: float for SOS_BF16 and SOS_FP32 (with SOS_BF16 only the core
+ * contractions run on tensor cores), double for SOS_FP64.  m: 1 .. 65536.
+ * Errors: SOS_E_INVALID for a plan with two_d != 4, a bad m or NULL pointers. */
+
+/* Bytes of the workspace a first-layer call needs (it contains a plan
+ * workspace of the same precision at offset 0, so sos_workspace_init applies). */
+int sos_layer_workspace_size(sos_plan_t plan, int prec, int m, size_t* bytes);
+
+/* A_hat (dev N x k) from B and A1. */
+int sos_layer_expand(sos_plan_t plan, int prec, int m, const void* B, const void* A1,
+                     void* A_hat, void* workspace, void* stream);
+
+/* loss = 1/2 ||c(A_hat(B, A1)) - p||^2 (dev double[2] = {loss, ||p||^2}, or
+ * NULL) and its gradients grad_B (dev k x nf*m) and grad_A1 (dev m x nf); a
+ * NULL gradient pointer skips that gradient. */
+int sos_layer_loss_grad(sos_plan_t plan, int prec, int m, const void* B, const void* A1,
+                        const void* p, void* grad_B, void* grad_A1, void* loss,
+                        void* workspace, void* stream);
+
+/* Optimiser state of the network, all dev and caller-owned: B, A1 updated in
+ * place; mB, vB (k x nf*m) and mA1, vA1 (m x nf) zero before the first Adam
+ * step; t = steps already taken.  flags: 0, or SOS_LAYER_FIXED_A1 to keep A1
+ * as it is (the paper's A = I comparison; mA1, vA1 may then be NULL). */
+typedef struct {
+    void* B;
+    void* mB;
+    void* vB;
+    void* A1;
+    void* mA1;
+    void* vA1;
+    int64_t t;
+    int32_t flags;
+    int32_t reserved;
+} sos_layer_state;
+
+#define SOS_LAYER_FIXED_A1 1
+
+/* One iteration: loss and gradients at (B, A1), then the update of B (and A1).
+ * opts as for sos_step (SOS_STEP_FP32_ADJOINT applies to the core adjoint of
+ * an SOS_FP64 step). */
+int sos_layer_step(sos_plan_t plan, int prec, int m, sos_layer_state* state, const void* p,
+                   const sos_step_opts* opts, void* loss, void* workspace, void* stream);
+
 /* ---- certificate (synchronous) ------------------------------------------ */
 
 /* FP64 certificate (Sec. 3: the error norm is about 1e-8 of the norm of the

@@ -12,6 +12,7 @@ Paper: Keren, Osadchy, Poranne, arXiv 2410.19844.
   * loss = 1/2 ||c(A) - p||^2 ..................... Eq. 2 (1/2 is our scale)
   * gradient by the chain rule .................... derived from Eq. 2
   * Adam, random init, best-error tracking ........ Sec. 3 (experimental set-up)
+  * the network ||B Z A1 x||^2 with its first layer  Sec. 2, Eq. 4, Sec. 2.1
 """
 from __future__ import annotations
 
@@ -231,11 +232,79 @@ class Oracle:
         x = np.ascontiguousarray(x, dtype=np.float64)
         return float(_load().oracle_eval(self.n, _ptr(self.Ed), self.N, _ptr(q), _ptr(x)))
 
+    # -- the network with its first layer (Sec. 2, Eq. 4) -----------------
+    def layer_expand(self, B, A1) -> np.ndarray:
+        """A_hat of the network on this table (dehomogenised when the table
+        has n = nf - 1 variables, homogeneous when it has nf)."""
+        nf = B.shape[1] // A1.shape[0]
+        return layer_expand(self.Ed, nf, B, A1)
+
+    def layer_coeffs(self, B, A1) -> np.ndarray:
+        return self.coeffs(self.layer_expand(B, A1))
+
+    def layer_loss_grad(self, B, A1, p):
+        """(loss, grad_B, grad_A1, c) of 1/2 ||c(A_hat(B, A1)) - p||^2: the
+        gradient with respect to A_hat, then the chain rule through
+        P_k = M_k A1 and the symmetrisation of P_k."""
+        B = np.asarray(B, dtype=np.float64)
+        A1 = np.asarray(A1, dtype=np.float64)
+        m = A1.shape[0]
+        nf = B.shape[1] // m
+        loss, g_hat, c = self.loss_grad(self.layer_expand(B, A1), p)
+        rows = form_rows(self.Ed, nf)
+        gB = np.zeros_like(B)
+        gA1 = np.zeros_like(A1)
+        for k in range(B.shape[0]):
+            S = g_hat[rows, k]                    # dL/dP_k, symmetric
+            Mk = B[k].reshape(nf, m)
+            gB[k] = (S @ A1.T).reshape(-1)
+            gA1 += Mk.T @ S
+        return loss, gB, gA1, c
+
     def certify(self, c, p) -> float:
         """Relative residual ||c - p||_2 / ||p||_2 in double precision."""
         c = np.asarray(c, dtype=np.float64)
         p = np.asarray(p, dtype=np.float64)
         return float(np.sqrt(2.0 * self.residual(c, p)[0]) / np.linalg.norm(p))
+
+
+def form_rows(Ed, nf: int) -> np.ndarray:
+    """rows[i, j] = row of the monomial x_i x_j (0 <= i, j < nf) in Ed.  Ed
+    with nf columns holds the form's monomials themselves; with nf - 1 columns
+    the form is dehomogenised: x_nf = 1, its exponent is 2 - |e|."""
+    Ed = np.asarray(Ed)
+    rows = np.full((nf, nf), -1, dtype=np.int64)
+    for a, e in enumerate(Ed):
+        e = [int(v) for v in e]
+        if len(e) == nf - 1:
+            e = e + [2 - sum(e)]
+        elif sum(e) != 2:
+            continue
+        i, j = [v for v in range(nf) for _ in range(e[v])]
+        rows[i, j] = rows[j, i] = a
+    assert (rows >= 0).all()
+    return rows
+
+
+def layer_expand(Ed, nf: int, B, A1) -> np.ndarray:
+    """Coefficient matrix A_hat (rows of Ed x k) of the network's form
+    ||B Z A1 x||^2 (Sec. 2, Eq. 4): Z A1 x stacks x_i (A1 x) for i = 1..nf, so
+    output k is x^T M_k A1 x with M_k = B[k] read as nf x m.  With P_k = M_k A1,
+    the coefficient of x_i x_j in output k is P_k[i][j] + P_k[j][i] (i < j) and
+    P_k[i][i] (i = j).  Rows of Ed that are no degree-2 form monomial stay 0."""
+    B = np.asarray(B, dtype=np.float64)
+    A1 = np.asarray(A1, dtype=np.float64)
+    m = A1.shape[0]
+    assert A1.shape[1] == nf and B.shape[1] == nf * m
+    rows = form_rows(Ed, nf)
+    iu, ju = np.triu_indices(nf)
+    out = np.zeros((len(Ed), B.shape[0]))
+    for k in range(B.shape[0]):
+        P = B[k].reshape(nf, m) @ A1
+        sym = P + P.T
+        vals = np.where(iu == ju, np.diag(P)[iu], sym[iu, ju])
+        out[rows[iu, ju], k] = vals
+    return out
 
 
 def sizes(n: int, two_d: int):

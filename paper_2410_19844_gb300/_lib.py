@@ -31,7 +31,8 @@ EXPORTS = [
     "sos_timing_reset", "sos_timing_report", "sos_loss_from_coeffs_static", "sos_solve_opts_default",
     "sos_solve", "sos_group_create", "sos_group_destroy", "sos_group_scratch_size", "sos_group_set",
     "sos_group_clear", "sos_group_sync", "sos_group_run", "sos_group_losses", "sos_group_state",
-    "sos_convert", "sos_group_set_lr", "sos_diag_bounded_wait", "sos_last_error",
+    "sos_convert", "sos_group_set_lr", "sos_diag_bounded_wait", "sos_layer_workspace_size",
+    "sos_layer_expand", "sos_layer_loss_grad", "sos_layer_step", "sos_last_error",
 ]
 
 
@@ -47,6 +48,15 @@ SOS_STEP_FP32_ADJOINT = 1
 class sos_step_opts(ctypes.Structure):
     _fields_ = [("optimizer", ctypes.c_int), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("flags", ctypes.c_int)]
+
+
+class sos_layer_state(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_void_p), ("mB", ctypes.c_void_p), ("vB", ctypes.c_void_p),
+                ("A1", ctypes.c_void_p), ("mA1", ctypes.c_void_p), ("vA1", ctypes.c_void_p),
+                ("t", ctypes.c_int64), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+SOS_LAYER_FIXED_A1 = 1
 
 
 class sos_state(ctypes.Structure):
@@ -128,6 +138,10 @@ def lib(auto_build: bool = True):
         "sos_group_state": [vp, i32, P(vp), P(vp), P(i64)],
         "sos_convert": [vp, i32, vp, i32, i64, vp],
         "sos_diag_bounded_wait": [ctypes.c_uint64, vp, vp],
+        "sos_layer_workspace_size": [vp, i32, i32, P(ctypes.c_size_t)],
+        "sos_layer_expand": [vp, i32, i32, vp, vp, vp, vp, vp],
+        "sos_layer_loss_grad": [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp],
+        "sos_layer_step": [vp, i32, i32, P(sos_layer_state), vp, P(sos_step_opts), vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -326,3 +340,21 @@ def sos_group_set_lr(group, slot, lr) -> None:
 
 def sos_diag_bounded_wait(limit_ns, status, stream) -> None:
     _check(lib().sos_diag_bounded_wait(limit_ns, status, stream))
+
+
+def sos_layer_workspace_size(plan, prec, m) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().sos_layer_workspace_size(plan, prec, m, ctypes.byref(n)))
+    return n.value
+
+
+def sos_layer_expand(plan, prec, m, B, A1, A_hat, ws, stream) -> None:
+    _check(lib().sos_layer_expand(plan, prec, m, B, A1, A_hat, ws, stream))
+
+
+def sos_layer_loss_grad(plan, prec, m, B, A1, p, grad_B, grad_A1, loss, ws, stream) -> None:
+    _check(lib().sos_layer_loss_grad(plan, prec, m, B, A1, p, grad_B, grad_A1, loss, ws, stream))
+
+
+def sos_layer_step(plan, prec, m, state: sos_layer_state, p, opts: sos_step_opts, loss, ws, stream) -> None:
+    _check(lib().sos_layer_step(plan, prec, m, ctypes.byref(state), p, ctypes.byref(opts), loss, ws, stream))

@@ -90,6 +90,11 @@ Workspace batched_layout(const sos_plan_s* p, int prec, int64_t batch) {
 
 }  // namespace
 
+int sos::core_loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad, void* loss, void* ws,
+                        cudaStream_t st, bool fp32_contraction) {
+    return loss_grad(p, prec, A, pv, grad, loss, ws, st, fp32_contraction);
+}
+
 extern "C" {
 
 int sos_workspace_init(sos_plan_t p, int prec, void* ws, void* stream) {

@@ -94,6 +94,11 @@ struct DeviceTables {
     // a * N + b with a <= b, the top bit set when a == b
     int32_t* pair_ptr = nullptr;
     int32_t* pair_pos = nullptr;
+    // first layer (two_d = 4 only, built on demand): form_rows[i * nf + j] is
+    // the row of the form's monomial x_i x_j (nf = n + 1 form variables, the
+    // last one dehomogenised to 1); form_pairs[a] = (i, j), i <= j, of row a
+    int32_t* form_rows = nullptr;
+    int2* form_pairs = nullptr;
 };
 
 }  // namespace sos
@@ -160,6 +165,13 @@ int launch_tc_adjoint_pair(const sos_plan_s* plan, const void* h16, const void* 
 int launch_tc_adjoint_update_pair(const sos_plan_s* plan, const void* h16, const void* a16_cur, void* a16_next,
                                   float* A, float* m, float* v, int optimizer, int64_t t, double lr, double b1,
                                   double b2, double eps, int32_t* status, cudaStream_t st);
+
+// ---- one pass of the objective (api.cu), shared with the first layer ----------
+
+// loss = 1/2 ||c(A) - p||^2 into `loss` (or the workspace), gradient 2 H(c - p) A
+// into `grad` when it is not NULL; `ws` is a workspace of workspace_layout(plan, prec).
+int core_loss_grad(sos_plan_s* plan, int prec, const void* A, const void* p, void* grad, void* loss, void* ws,
+                   cudaStream_t st, bool fp32_contraction);
 
 // Whether the tensor-core contractions run on CTA pairs (environment variable
 // SOS_CTA_PAIRS = 0 or 1, read once; pairs by default).

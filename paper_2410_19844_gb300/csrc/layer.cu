@@ -1,0 +1,395 @@
+// The paper's network with its first layer (Sec. 2, Sec. 2.1): the quartic form
+// ||B Z A1 x||^2 in nf = n + 1 variables.
+//
+// A1 (m x nf) is the linear first layer, v = A1 x; Z multiplies v by every x_i,
+// giving the nf*m entries x_i v_j (index i*m + j); B (k x nf*m) forms k outputs.
+// Output k is therefore the quadratic form x^T M_k A1 x with M_k[i][j] =
+// B[k][i*m + j], i.e. B read as a stack of nf x m blocks.  Writing P_k = M_k A1
+// (nf x nf), the form is sum_k (x^T P_k x)^2, whose coefficient matrix over the
+// degree-2 monomials x_i x_j (i <= j) has entries
+//     A_hat[(i, j)][k] = P_k[i][j] + P_k[j][i]  (i < j),   P_k[i][i]  (i = j).
+// The plan's degree-<=4 basis in n = nf - 1 variables is the form dehomogenised
+// (x_nf = 1), so A_hat is the plan's N x k coefficient matrix and the loss and
+// its gradient with respect to A_hat are the core pass.  The gradient comes
+// back through the expansion by the chain rule:
+//     dL/dP_k[i][j] = dL/dA_hat[(min, max)(i, j)][k]      (the symmetric S_k)
+//     dL/dB (as the stack of M_k) = S A1^T,   dL/dA1 = sum_k M_k^T S_k,
+// three plain GEMMs with B viewed as a (k nf) x m matrix.  They are small next
+// to the core pass (k nf^2 m against k N^2 multiply-adds) and run on CUDA cores
+// in the step's precision (float for BF16 and FP32, double for FP64).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace sos {
+namespace {
+
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+// C = A B with A(i, l) = A[i * as0 + l * as1] and B(l, j) = B[l * bs0 + j * bs1];
+// grid (ceil(Ncol / 64), ceil(M / 64), splits).  Split z covers l in
+// [z * kchunk, (z + 1) * kchunk) and writes its own M x Ncol block of C (at
+// C + z * split_stride), summed afterwards by split_sum_kernel in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) strided_gemm_kernel(int64_t M, int64_t Ncol, int64_t K, int64_t kchunk,
+                                                           const T* __restrict__ A, int64_t as0, int64_t as1,
+                                                           const T* __restrict__ B, int64_t bs0, int64_t bs1,
+                                                           T* __restrict__ C, int64_t ldc, int64_t split_stride) {
+    __shared__ T As[kBK][kBM + 1];
+    __shared__ T Bs[kBK][kBN + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t i0 = (int64_t)blockIdx.y * kBM, j0 = (int64_t)blockIdx.x * kBN;
+    const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+    const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kBK) {
+        // stage both tiles, walking the operand's contiguous dimension fastest
+        for (int e = threadIdx.x; e < kBM * kBK; e += 256) {
+            int ii, kk;
+            if (as1 == 1) {
+                ii = e / kBK;
+                kk = e % kBK;
+            } else {
+                kk = e / kBM;
+                ii = e % kBM;
+            }
+            const int64_t gi = i0 + ii, gk = k0 + kk;
+            As[kk][ii] = (gi < M && gk < kend) ? A[gi * as0 + gk * as1] : T(0);
+        }
+        for (int e = threadIdx.x; e < kBN * kBK; e += 256) {
+            int jj, kk;
+            if (bs1 == 1) {
+                kk = e / kBN;
+                jj = e % kBN;
+            } else {
+                jj = e / kBK;
+                kk = e % kBK;
+            }
+            const int64_t gj = j0 + jj, gk = k0 + kk;
+            Bs[kk][jj] = (gj < Ncol && gk < kend) ? B[gk * bs0 + gj * bs1] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+    T* Cz = C + (int64_t)blockIdx.z * split_stride;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + ty + 16 * u;
+        if (i >= M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t j = j0 + tx + 16 * v;
+            if (j < Ncol) Cz[i * ldc + j] = acc[u][v];
+        }
+    }
+}
+
+// C[i][j] = sum over z = 0, 1, ... of part[z][i][j], in that order.
+template <typename T>
+__global__ void split_sum_kernel(const T* __restrict__ part, int splits, int64_t M, int64_t Ncol,
+                                 T* __restrict__ C, int64_t ldc) {
+    const int64_t count = M * Ncol;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int z = 0; z < splits; ++z) s += part[(int64_t)z * count + e];
+        C[(e / Ncol) * ldc + e % Ncol] = s;
+    }
+}
+
+// A_hat[a][kk] = P_kk[i][j] + P_kk[j][i] (i < j) or P_kk[i][i], (i, j) = pairs[a].
+template <typename T>
+__global__ void form_expand_kernel(const T* __restrict__ P, const int2* __restrict__ pairs, int64_t N, int64_t k,
+                                   int nf, T* __restrict__ Ahat) {
+    const int64_t count = N * k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = e / k, kk = e % k;
+        const int2 ij = pairs[a];
+        const T* Pk = P + kk * nf * nf;
+        T v = Pk[ij.x * nf + ij.y];
+        if (ij.x != ij.y) v += Pk[ij.y * nf + ij.x];
+        Ahat[e] = v;
+    }
+}
+
+// S_kk[i][j] = G[rows[i][j]][kk] for every (i, j): the gradient with respect to
+// P_kk, symmetric because x_i x_j and x_j x_i are one monomial.
+template <typename T>
+__global__ void form_scatter_kernel(const T* __restrict__ G, const int32_t* __restrict__ rows, int64_t k, int nf,
+                                    T* __restrict__ S) {
+    const int64_t count = k * nf * nf;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kk = e / ((int64_t)nf * nf);
+        const int ij = (int)(e % ((int64_t)nf * nf));
+        S[e] = G[(int64_t)rows[ij] * k + kk];
+    }
+}
+
+int grid_for(int64_t count) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 16));
+}
+
+// Split count for a GEMM whose output has `tiles` tiles and depth K: enough
+// blocks for two waves on 152 SMs, each split at least a few K-slices deep.
+int split_count(int64_t tiles, int64_t K) {
+    const int64_t want = std::max<int64_t>(1, 304 / std::max<int64_t>(1, tiles));
+    const int64_t most = std::max<int64_t>(1, K / (4 * kBK));
+    return (int)std::min<int64_t>(std::min<int64_t>(want, most), 1024);
+}
+
+struct LayerLayout {
+    size_t core = 0;    // the plan's workspace for prec, at offset 0
+    size_t P = 0;       // k x nf x nf: P_k, then S_k
+    size_t Ahat = 0;    // N x k
+    size_t gAhat = 0;   // N x k
+    size_t gB = 0;      // k x nf*m
+    size_t gA1 = 0;     // m x nf
+    size_t part = 0;    // split partial sums of dL/dA1
+    size_t total = 0;
+    int splits = 1;
+    int64_t kchunk = 0;
+};
+
+LayerLayout layer_layout(const sos_plan_s* p, int prec, int m) {
+    LayerLayout w;
+    const size_t elt = prec == SOS_FP64 ? 8 : 4;
+    const int64_t nf = p->n + 1, k = p->r;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t a = off;
+        off += (bytes + 255) / 256 * 256;
+        return a;
+    };
+    w.core = take(workspace_layout(p, prec).total);
+    w.P = take((size_t)k * nf * nf * elt);
+    w.Ahat = take((size_t)p->N * k * elt);
+    w.gAhat = take((size_t)p->N * k * elt);
+    w.gB = take((size_t)k * nf * m * elt);
+    w.gA1 = take((size_t)m * nf * elt);
+    const int64_t K = k * nf;
+    const int64_t tiles = ((m + kBM - 1) / kBM) * ((nf + kBN - 1) / kBN);
+    w.splits = split_count(tiles, K);
+    w.kchunk = ((K + w.splits - 1) / w.splits + kBK - 1) / kBK * kBK;
+    w.splits = (int)((K + w.kchunk - 1) / w.kchunk);
+    w.part = take((size_t)w.splits * m * nf * elt);
+    w.total = off;
+    return w;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+int check_layer(sos_plan_s* p, int prec, int m, const char* who) {
+    if (!p || prec < SOS_BF16 || prec > SOS_FP64) return fail(SOS_E_INVALID, std::string(who) + ": bad plan or precision");
+    if (p->two_d != 4)
+        return fail(SOS_E_INVALID, std::string(who) + ": the first layer produces quartics; the plan needs two_d = 4");
+    if (m < 1 || m > 65536) return fail(SOS_E_INVALID, std::string(who) + ": need 1 <= m <= 65536");
+    return SOS_OK;
+}
+
+// Row of x_i x_j (0 <= i, j < nf) in the plan's degree-<=2 table.
+int ensure_form_tables(sos_plan_s* p) {
+    SOS_CHECK(ensure_device(p));
+    std::lock_guard<std::mutex> lock(p->mu);
+    if (p->dev.form_rows) return SOS_OK;
+    const int n = p->n, nf = n + 1;
+    std::vector<int32_t> rows((size_t)nf * nf, -1);
+    std::vector<int2> pairs((size_t)p->N);
+    for (int64_t a = 0; a < p->N; ++a) {
+        const uint8_t* e = &p->Ed[(size_t)a * n];
+        int v[2], c = 0, deg = 0;
+        for (int j = 0; j < n; ++j)
+            for (int t = 0; t < e[j]; ++t) v[c++] = j;
+        deg = c;
+        for (; c < 2; ++c) v[c] = n;          // the dehomogenised variable x_nf = 1
+        if (deg > 2) return fail(SOS_E_INVALID, "first layer: plan rows of degree > 2");
+        rows[(size_t)v[0] * nf + v[1]] = (int32_t)a;
+        rows[(size_t)v[1] * nf + v[0]] = (int32_t)a;
+        pairs[a] = make_int2(v[0], v[1]);
+    }
+    for (int32_t r : rows)
+        if (r < 0) return fail(SOS_E_INVALID, "first layer: plan rows do not cover the degree-2 forms");
+    int32_t* d_rows = nullptr;
+    int2* d_pairs = nullptr;
+    cudaError_t e = cudaMalloc(&d_rows, rows.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_pairs, pairs.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMemcpy(d_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_rows);
+        cudaFree(d_pairs);
+        return cuda_fail(e, "first layer: tables");
+    }
+    p->dev.form_rows = d_rows;
+    p->dev.form_pairs = d_pairs;
+    return SOS_OK;
+}
+
+template <typename T>
+int launch_gemm(int64_t M, int64_t Ncol, int64_t K, int64_t kchunk, int splits, const T* A, int64_t as0, int64_t as1,
+                const T* B, int64_t bs0, int64_t bs1, T* C, int64_t ldc, int64_t split_stride, cudaStream_t st) {
+    if ((M + kBM - 1) / kBM > 65535 || (Ncol + kBN - 1) / kBN > 65535)
+        return fail(SOS_E_UNSUPPORTED, "first layer: k (n + 1) or m too large for one GEMM grid");
+    dim3 grid((unsigned)((Ncol + kBN - 1) / kBN), (unsigned)((M + kBM - 1) / kBM), (unsigned)splits);
+    KernelScope ks_("layer_gemm", st);
+    strided_gemm_kernel<T><<<grid, 256, 0, st>>>(M, Ncol, K, kchunk, A, as0, as1, B, bs0, bs1, C, ldc, split_stride);
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+// P_k = M_k A1 for every k, then A_hat.
+template <typename T>
+int expand(sos_plan_s* p, int m, const T* B, const T* A1, T* Ahat, const LayerLayout& w, void* ws, cudaStream_t st) {
+    const int64_t nf = p->n + 1, k = p->r;
+    T* P = at<T>(ws, w.P);
+    // (k nf) x m times m x nf
+    SOS_CHECK(launch_gemm<T>(k * nf, nf, m, m, 1, B, m, 1, A1, nf, 1, P, nf, 0, st));
+    {
+        KernelScope ks_("layer_expand", st);
+        form_expand_kernel<T><<<grid_for(p->N * k), 256, 0, st>>>(P, p->dev.form_pairs, p->N, k, (int)nf, Ahat);
+    }
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+// dL/dB and dL/dA1 from dL/dA_hat (either output may be NULL).
+template <typename T>
+int pull_back(sos_plan_s* p, int m, const T* B, const T* A1, const T* gAhat, T* gB, T* gA1, const LayerLayout& w,
+              void* ws, cudaStream_t st) {
+    const int64_t nf = p->n + 1, k = p->r;
+    T* S = at<T>(ws, w.P);
+    {
+        KernelScope ks_("layer_scatter", st);
+        form_scatter_kernel<T><<<grid_for(k * nf * nf), 256, 0, st>>>(gAhat, p->dev.form_rows, k, (int)nf, S);
+    }
+    SOS_CUDA(cudaGetLastError());
+    if (gB)   // S (k nf x nf) times A1^T (nf x m)
+        SOS_CHECK(launch_gemm<T>(k * nf, m, nf, nf, 1, S, nf, 1, A1, 1, nf, gB, m, 0, st));
+    if (gA1) {  // B^T (m x k nf) times S (k nf x nf), split along k nf
+        T* part = at<T>(ws, w.part);
+        SOS_CHECK(launch_gemm<T>(m, nf, k * nf, w.kchunk, w.splits, B, 1, m, S, nf, 1, part, nf, (int64_t)m * nf, st));
+        KernelScope ks_("layer_split_sum", st);
+        split_sum_kernel<T><<<grid_for((int64_t)m * nf), 256, 0, st>>>(part, w.splits, m, nf, gA1, nf);
+        SOS_CUDA(cudaGetLastError());
+    }
+    return SOS_OK;
+}
+
+template <typename T>
+int layer_loss_grad(sos_plan_s* p, int prec, int m, const void* B, const void* A1, const void* pv, void* gB, void* gA1,
+                    void* loss, void* ws, cudaStream_t st, bool fp32_contraction) {
+    const LayerLayout w = layer_layout(p, prec, m);
+    T* Ahat = at<T>(ws, w.Ahat);
+    T* gAhat = (gB || gA1) ? at<T>(ws, w.gAhat) : nullptr;
+    SOS_CHECK(expand<T>(p, m, static_cast<const T*>(B), static_cast<const T*>(A1), Ahat, w, ws, st));
+    SOS_CHECK(core_loss_grad(p, prec, Ahat, pv, gAhat, loss, at<char>(ws, w.core), st, fp32_contraction));
+    if (gAhat)
+        SOS_CHECK(pull_back<T>(p, m, static_cast<const T*>(B), static_cast<const T*>(A1), gAhat, static_cast<T*>(gB),
+                               static_cast<T*>(gA1), w, ws, st));
+    return SOS_OK;
+}
+
+}  // namespace
+}  // namespace sos
+
+using namespace sos;
+
+extern "C" {
+
+int sos_layer_workspace_size(sos_plan_t p, int prec, int m, size_t* bytes) {
+    SOS_CHECK(check_layer(p, prec, m, "sos_layer_workspace_size"));
+    if (!bytes) return fail(SOS_E_INVALID, "sos_layer_workspace_size: NULL output");
+    *bytes = layer_layout(p, prec, m).total;
+    return SOS_OK;
+}
+
+int sos_layer_expand(sos_plan_t p, int prec, int m, const void* B, const void* A1, void* A_hat, void* ws,
+                     void* stream) {
+    TraceRange trace_("sos_layer_expand");
+    SOS_CHECK(check_layer(p, prec, m, "sos_layer_expand"));
+    if (!B || !A1 || !A_hat || !ws) return fail(SOS_E_INVALID, "sos_layer_expand: NULL argument");
+    SOS_CHECK(ensure_form_tables(p));
+    cudaStream_t st = (cudaStream_t)stream;
+    const LayerLayout w = layer_layout(p, prec, m);
+    if (prec == SOS_FP64)
+        return expand<double>(p, m, static_cast<const double*>(B), static_cast<const double*>(A1),
+                              static_cast<double*>(A_hat), w, ws, st);
+    return expand<float>(p, m, static_cast<const float*>(B), static_cast<const float*>(A1), static_cast<float*>(A_hat),
+                         w, ws, st);
+}
+
+int sos_layer_loss_grad(sos_plan_t p, int prec, int m, const void* B, const void* A1, const void* pv, void* grad_B,
+                        void* grad_A1, void* loss, void* ws, void* stream) {
+    TraceRange trace_("sos_layer_loss_grad");
+    SOS_CHECK(check_layer(p, prec, m, "sos_layer_loss_grad"));
+    if (!B || !A1 || !pv || !ws) return fail(SOS_E_INVALID, "sos_layer_loss_grad: NULL argument");
+    SOS_CHECK(ensure_form_tables(p));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == SOS_FP64) return layer_loss_grad<double>(p, prec, m, B, A1, pv, grad_B, grad_A1, loss, ws, st, false);
+    return layer_loss_grad<float>(p, prec, m, B, A1, pv, grad_B, grad_A1, loss, ws, st, false);
+}
+
+int sos_layer_step(sos_plan_t p, int prec, int m, sos_layer_state* s, const void* pv, const sos_step_opts* o,
+                   void* loss, void* ws, void* stream) {
+    TraceRange trace_("sos_layer_step");
+    SOS_CHECK(check_layer(p, prec, m, "sos_layer_step"));
+    if (!s || !o || !s->B || !s->A1 || !pv || !ws) return fail(SOS_E_INVALID, "sos_layer_step: NULL argument");
+    if (o->optimizer != SOS_ADAM && o->optimizer != SOS_GD) return fail(SOS_E_INVALID, "sos_layer_step: bad optimizer");
+    const bool fixed = (s->flags & SOS_LAYER_FIXED_A1) != 0;
+    if (o->optimizer == SOS_ADAM && (!s->mB || !s->vB || (!fixed && (!s->mA1 || !s->vA1))))
+        return fail(SOS_E_INVALID, "sos_layer_step: Adam needs m and v for every trained matrix");
+    if (o->flags & ~SOS_STEP_FP32_ADJOINT) return fail(SOS_E_INVALID, "sos_layer_step: unknown flags");
+    if (s->flags & ~SOS_LAYER_FIXED_A1) return fail(SOS_E_INVALID, "sos_layer_step: unknown state flags");
+    SOS_CHECK(ensure_form_tables(p));
+    cudaStream_t st = (cudaStream_t)stream;
+    const LayerLayout w = layer_layout(p, prec, m);
+    const int64_t nf = p->n + 1, k = p->r, t = s->t + 1;
+    const bool fp32c = prec == SOS_FP64 && (o->flags & SOS_STEP_FP32_ADJOINT);
+    if (prec == SOS_FP64) {
+        double* gB = at<double>(ws, w.gB);
+        double* gA1 = fixed ? nullptr : at<double>(ws, w.gA1);
+        SOS_CHECK(layer_loss_grad<double>(p, prec, m, s->B, s->A1, pv, gB, gA1, loss, ws, st, fp32c));
+        SOS_CHECK(launch_update<double>(k, nf * m, static_cast<double*>(s->B), static_cast<double*>(s->mB),
+                                        static_cast<double*>(s->vB), gB, o->optimizer, t, o->lr, o->beta1, o->beta2,
+                                        o->eps, nullptr, 0, st));
+        if (!fixed)
+            SOS_CHECK(launch_update<double>(m, nf, static_cast<double*>(s->A1), static_cast<double*>(s->mA1),
+                                            static_cast<double*>(s->vA1), gA1, o->optimizer, t, o->lr, o->beta1,
+                                            o->beta2, o->eps, nullptr, 0, st));
+    } else {
+        float* gB = at<float>(ws, w.gB);
+        float* gA1 = fixed ? nullptr : at<float>(ws, w.gA1);
+        SOS_CHECK(layer_loss_grad<float>(p, prec, m, s->B, s->A1, pv, gB, gA1, loss, ws, st, false));
+        SOS_CHECK(launch_update<float>(k, nf * m, static_cast<float*>(s->B), static_cast<float*>(s->mB),
+                                       static_cast<float*>(s->vB), gB, o->optimizer, t, o->lr, o->beta1, o->beta2,
+                                       o->eps, nullptr, 0, st));
+        if (!fixed)
+            SOS_CHECK(launch_update<float>(m, nf, static_cast<float*>(s->A1), static_cast<float*>(s->mA1),
+                                           static_cast<float*>(s->vA1), gA1, o->optimizer, t, o->lr, o->beta1,
+                                           o->beta2, o->eps, nullptr, 0, st));
+    }
+    s->t = t;
+    return SOS_OK;
+}
+
+}  // extern "C"

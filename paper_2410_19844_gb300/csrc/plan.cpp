@@ -169,6 +169,8 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.adj_tiles2);
         cudaFree(p->dev.pair_ptr);
         cudaFree(p->dev.pair_pos);
+        cudaFree(p->dev.form_rows);
+        cudaFree(p->dev.form_pairs);
         if (cur >= 0) cudaSetDevice(cur);
     }
     delete p;

@@ -185,3 +185,85 @@ class Optimizer:
         L.sos_step(self.plan.handle, self.prec, self.state, _ptr(p), self.opts, _ptr(self.loss),
                    _ptr(self.plan.workspace(self.prec, self.A.device)), _stream_handle())
         return self.loss
+
+
+class Layer:
+    """The network of Sec. 2 with its first layer: the quartic form
+    ||B Z A1 x||^2 in n + 1 variables (A1: m x (n+1), B: k x (n+1) m), on a
+    plan with two_d = 4 and r = k.  Every computation is a call into the
+    library (sos_layer_*)."""
+
+    def __init__(self, plan: Plan, m: int):
+        if plan.two_d != 4:
+            raise ValueError("the first layer produces quartics: the plan needs two_d = 4")
+        self.plan, self.m, self.nf, self.k = plan, int(m), plan.n + 1, plan.r
+        self._ws = {}
+
+    def workspace(self, prec, device=None) -> torch.Tensor:
+        prec = _prec(prec)
+        ws = self._ws.get(prec)
+        if ws is None:
+            nbytes = L.sos_layer_workspace_size(self.plan.handle, prec, self.m)
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=torch.device(device or "cuda"))
+            L.sos_workspace_init(self.plan.handle, prec, _ptr(ws), _stream_handle())
+            self._ws[prec] = ws
+        return ws
+
+    def _check(self, B: torch.Tensor, A1: torch.Tensor, prec: int):
+        dt = _DTYPE[prec]
+        for name, t, shape in (("B", B, (self.k, self.nf * self.m)), ("A1", A1, (self.m, self.nf))):
+            if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor")
+            if tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be {shape}, got {tuple(t.shape)}")
+
+    def expand(self, B: torch.Tensor, A1: torch.Tensor, prec="fp32") -> torch.Tensor:
+        """The plan's coefficient matrix A_hat (N x k) of the network."""
+        prec = _prec(prec)
+        self._check(B, A1, prec)
+        A_hat = torch.empty(self.plan.N, self.k, dtype=_DTYPE[prec], device=B.device)
+        L.sos_layer_expand(self.plan.handle, prec, self.m, _ptr(B), _ptr(A1), _ptr(A_hat),
+                           _ptr(self.workspace(prec, B.device)), _stream_handle())
+        return A_hat
+
+    def loss_grad(self, B: torch.Tensor, A1: torch.Tensor, p: torch.Tensor, prec="fp32", want_grad=True):
+        """(loss, ||p||^2, grad_B, grad_A1) with loss = 1/2 ||c - p||^2."""
+        prec = _prec(prec)
+        self._check(B, A1, prec)
+        out = torch.empty(2, dtype=torch.float64, device=B.device)
+        gB = torch.empty_like(B) if want_grad else None
+        gA1 = torch.empty_like(A1) if want_grad else None
+        L.sos_layer_loss_grad(self.plan.handle, prec, self.m, _ptr(B), _ptr(A1), _ptr(p), _ptr(gB), _ptr(gA1),
+                              _ptr(out), _ptr(self.workspace(prec, B.device)), _stream_handle())
+        return out[0], out[1], gB, gA1
+
+
+class LayerOptimizer:
+    """Adam (or GD) on the network's B and A1 through sos_layer_step; with
+    fixed_A1 the first layer stays as it is (the paper's A = I comparison)."""
+
+    def __init__(self, layer: Layer, B: torch.Tensor, A1: torch.Tensor, prec="fp32", optimizer="adam", lr=1e-2,
+                 beta1=0.9, beta2=0.999, eps=1e-8, fixed_A1=False, fp32_adjoint=False):
+        self.layer, self.prec = layer, _prec(prec)
+        layer._check(B, A1, self.prec)
+        self.B, self.A1 = B, A1
+        self.opts = L.sos_step_opts(L.SOS_ADAM if optimizer == "adam" else L.SOS_GD, lr, beta1, beta2, eps,
+                                    L.SOS_STEP_FP32_ADJOINT if fp32_adjoint else 0)
+        adam = optimizer == "adam"
+        self.mB = torch.zeros_like(B) if adam else None
+        self.vB = torch.zeros_like(B) if adam else None
+        self.mA1 = torch.zeros_like(A1) if adam and not fixed_A1 else None
+        self.vA1 = torch.zeros_like(A1) if adam and not fixed_A1 else None
+        self.state = L.sos_layer_state(_ptr(B), _ptr(self.mB), _ptr(self.vB), _ptr(A1), _ptr(self.mA1),
+                                       _ptr(self.vA1), 0, L.SOS_LAYER_FIXED_A1 if fixed_A1 else 0, 0)
+        self.loss = torch.zeros(2, dtype=torch.float64, device=B.device)
+
+    @property
+    def t(self) -> int:
+        return self.state.t
+
+    def step(self, p: torch.Tensor) -> torch.Tensor:
+        """One iteration; returns the device tensor {loss before the step, ||p||^2}."""
+        L.sos_layer_step(self.layer.plan.handle, self.prec, self.layer.m, self.state, _ptr(p), self.opts,
+                         _ptr(self.loss), _ptr(self.layer.workspace(self.prec, self.B.device)), _stream_handle())
+        return self.loss

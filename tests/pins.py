@@ -88,6 +88,14 @@ def quartic_identity_coeffs(Ed, E2d, A) -> np.ndarray:
         v = A[row[tuple(e)]]
         return 2.0 * v if i == j else v
 
+    return quartic_identities(E2d, f)
+
+
+def quartic_identities(E2d, f) -> np.ndarray:
+    """The five identities of Sec. 2 for the degree-4 entries of E2d, given
+    f(i, j) = the vector of second derivatives of the outputs by x_i, x_j."""
+    n = E2d.shape[1]
+
     def ip(u, w):
         return float(np.dot(u, w))
 
@@ -116,6 +124,22 @@ def quartic_identity_coeffs(Ed, E2d, A) -> np.ndarray:
             out[g] = 2.0 * (ip(f(i, j), f(k, l)) + ip(f(i, k), f(j, l))
                             + ip(f(i, l), f(j, k)))
     return out
+
+
+def network_second_derivative(B, A1, i, j) -> np.ndarray:
+    """f_{x_i x_j} of the network f = B Z A1 x (Sec. 2): B Z_{x_i} A1 x_{x_j} +
+    B Z_{x_j} A1 x_{x_i}, where Z_{x_i} keeps only the i-th identity block, so
+    each term is the i-th block of columns of B times column j of A1."""
+    m = A1.shape[0]
+    return B[:, i * m:(i + 1) * m] @ A1[:, j] + B[:, j * m:(j + 1) * m] @ A1[:, i]
+
+
+def network_value(B, A1, x) -> float:
+    """||B Z A1 x||^2 evaluated literally: Z stacks x_i times the m x m identity."""
+    m = A1.shape[0]
+    Z = np.kron(x[:, None], np.eye(m))          # (nf m) x m, block i = x_i I
+    f = B @ (Z @ (A1 @ x))
+    return float(np.dot(f, f))
 
 
 def general_rule_coeff(Ed, A, gamma) -> float:
