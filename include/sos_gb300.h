@@ -58,7 +58,22 @@ typedef enum {
     SOS_E_UNSUPPORTED = -6   /* the request is valid but not implemented here */
 } sos_status;
 
-typedef enum { SOS_BF16 = 0, SOS_FP32 = 1, SOS_FP64 = 2 } sos_prec;
+/* Precisions.  SOS_BF16: FP32 data, contractions on tensor cores from bf16
+ * operands.  SOS_FP32, SOS_FP64: CUDA cores.  SOS_FP64_TC: FP64 data; the
+ * forward c(A) is computed on tensor cores by the slicing method of
+ * Ozaki et al. (error-free splitting of a matrix product): each row of A is
+ * scaled by a power of two and cut into 5-bit integer slices, held exactly in
+ * bf16; every product of two slices is exact in the tensor core's FP32
+ * accumulator while r * 31^2 < 2^24 (r <= 17,458), and the products are
+ * scaled and summed in FP64.  With s slices (sos_step_opts.slices, 8 by
+ * default) each term A[a][k] A[b][k] is off by at most (s + 2) 2^(-5 s)
+ * 2^(e_a + e_b), e_a the exponent of row a's largest entry: about 1e-11 of
+ * the rows' scales for 8 slices.  The residual and loss are FP64; the adjoint
+ * runs on tensor cores from bf16 H(r) and bf16 A (its error is proportional
+ * to the residual, so iterations still converge to the exact fit); the update
+ * is FP64.  Supported by sos_coeffs, sos_loss_grad (grad is double), sos_step
+ * and sos_solve; other calls reject it with SOS_E_INVALID. */
+typedef enum { SOS_BF16 = 0, SOS_FP32 = 1, SOS_FP64 = 2, SOS_FP64_TC = 3 } sos_prec;
 typedef enum { SOS_ADAM = 0, SOS_GD = 1 } sos_opt;
 typedef enum {
     SOS_VERDICT_ERROR = -1,
@@ -154,6 +169,9 @@ typedef struct {
     double lr;
     double beta1, beta2, eps;
     int flags;          /* 0, or SOS_STEP_FP32_ADJOINT */
+    int slices;         /* SOS_FP64_TC: 5-bit slices of A, 2..8 (0 = 8): each term of the
+                           forward is off by at most (slices + 2) 2^(-5 slices) of its rows'
+                           scales; it costs slices (slices + 1) / 2 tensor-core passes */
 } sos_step_opts;
 
 /* With SOS_FP64: contract the adjoint 2 H(r) A in FP32 from the FP64
@@ -282,6 +300,12 @@ typedef struct {
     double cert_tol;          /* certificate threshold (Sec. 3: about 1e-8) */
     int start_prec;           /* SOS_BF16 (the ladder), SOS_FP32 (no BF16
                                  stage) or SOS_FP64 (FP64 steps only) */
+    int tc_fp64;              /* 1: after the BF16 stage, SOS_FP64_TC steps take the
+                                 place of the FP32 and FP64 stages (up to fp64_steps,
+                                 or until stall_checks checks without a 1% gain),
+                                 with slices chosen from the current residual so the
+                                 forward stays about 2^-10 of it; the certificate is
+                                 still the CUDA-core FP64 evaluation */
 } sos_solve_opts;
 
 typedef struct {

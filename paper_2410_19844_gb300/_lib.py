@@ -17,11 +17,11 @@ SOS_E_TIMEOUT = -4
 SOS_E_NONFINITE = -5
 SOS_E_UNSUPPORTED = -6
 
-SOS_BF16, SOS_FP32, SOS_FP64 = 0, 1, 2
+SOS_BF16, SOS_FP32, SOS_FP64, SOS_FP64_TC = 0, 1, 2, 3
 SOS_ADAM, SOS_GD = 0, 1
 SOS_VERDICT_ERROR, SOS_VERDICT_NOT_CONVERGED, SOS_VERDICT_SOS = -1, 0, 1
 
-PREC = {"bf16": SOS_BF16, "fp32": SOS_FP32, "fp64": SOS_FP64}
+PREC = {"bf16": SOS_BF16, "fp32": SOS_FP32, "fp64": SOS_FP64, "fp64_tc": SOS_FP64_TC}
 
 EXPORTS = [
     "sos_plan_create", "sos_plan_destroy", "sos_plan_sizes", "sos_plan_monomials", "sos_plan_idx",
@@ -47,7 +47,8 @@ SOS_STEP_FP32_ADJOINT = 1
 
 class sos_step_opts(ctypes.Structure):
     _fields_ = [("optimizer", ctypes.c_int), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
-                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("flags", ctypes.c_int)]
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("flags", ctypes.c_int),
+                ("slices", ctypes.c_int)]
 
 
 class sos_layer_state(ctypes.Structure):
@@ -70,7 +71,7 @@ class sos_solve_opts(ctypes.Structure):
                 ("eps", ctypes.c_double), ("max_steps", ctypes.c_int64), ("check_every", ctypes.c_int64),
                 ("switch_rel", ctypes.c_double), ("stall_checks", ctypes.c_int64),
                 ("fp64_steps", ctypes.c_int64), ("fp64_fp32_adjoint", ctypes.c_int),
-                ("cert_tol", ctypes.c_double), ("start_prec", ctypes.c_int)]
+                ("cert_tol", ctypes.c_double), ("start_prec", ctypes.c_int), ("tc_fp64", ctypes.c_int)]
 
 
 class sos_result(ctypes.Structure):

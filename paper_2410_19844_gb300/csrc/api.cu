@@ -16,16 +16,40 @@ T* at(void* ws, size_t off) {
     return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
 }
 
-bool bad_prec(int prec) { return prec < SOS_BF16 || prec > SOS_FP64; }
+bool bad_prec(int prec) { return prec < SOS_BF16 || prec > SOS_FP64_TC; }
 
 int check_ptr(const void* p, const char* what) {
     if (!p) return fail(SOS_E_INVALID, std::string(what) + " is NULL");
     return SOS_OK;
 }
 
+// SOS_FP64_TC: forward on tensor cores by slices, FP64 residual and loss, and
+// (when g32 is not NULL) the adjoint 2 H(r) A on tensor cores from bf16 H and
+// bf16 A into the float buffer g32.
+int pass_tc64(sos_plan_s* p, const double* A, const double* pv, float* g32, void* loss, void* ws, cudaStream_t st,
+              int slices) {
+    const Workspace w = workspace_layout(p, SOS_FP64_TC);
+    double* c = at<double>(ws, w.c);
+    SOS_CHECK(forward_tc64(p, A, ws, c, slices, st));
+    double* L = loss ? static_cast<double*>(loss) : at<double>(ws, w.loss);
+    int32_t* status = at<int32_t>(ws, w.status);
+    double* resid = at<double>(ws, w.resid);
+    SOS_CHECK(launch_residual<double>(p, c, pv, resid, L, at<double>(ws, w.partials), status, 1, st));
+    if (!g32) return SOS_OK;
+    float* r32 = at<float>(ws, w.resid32);
+    SOS_CHECK(launch_convert<double, float>(resid, r32, p->M, st));
+    SOS_CHECK(launch_build_h16(p, r32, at<char>(ws, w.h16), st));
+    SOS_CHECK(launch_cast_bf16_from_double(A, p->N, p->r, at<char>(ws, w.a16), p->ld16, st));
+    return launch_tc_adjoint_pair(p, at<char>(ws, w.h16), at<char>(ws, w.a16), g32, status, st);
+}
+
 // Forward into ws.c (zeroed here).  For BF16 also writes the bf16 copy of A.
 int forward(sos_plan_s* p, int prec, const void* A, void* ws, cudaStream_t st, void* c_out) {
     const Workspace w = workspace_layout(p, prec);
+    if (prec == SOS_FP64_TC) {
+        double* c = c_out ? static_cast<double*>(c_out) : at<double>(ws, w.c);
+        return forward_tc64(p, static_cast<const double*>(A), ws, c, kMaxSlices, st);
+    }
     if (prec == SOS_FP64) {
         double* c = c_out ? static_cast<double*>(c_out) : at<double>(ws, w.c);
         SOS_CUDA(cudaMemsetAsync(c, 0, (size_t)p->M * sizeof(double), st));
@@ -43,6 +67,13 @@ int forward(sos_plan_s* p, int prec, const void* A, void* ws, cudaStream_t st, v
 int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad, void* loss, void* ws,
               cudaStream_t st, bool fp32_contraction = false) {
     const Workspace w = workspace_layout(p, prec);
+    if (prec == SOS_FP64_TC) {
+        float* g32 = grad ? at<float>(ws, w.grad) : nullptr;
+        SOS_CHECK(pass_tc64(p, static_cast<const double*>(A), static_cast<const double*>(pv), g32, loss, ws, st,
+                            kMaxSlices));
+        if (grad) SOS_CHECK(launch_convert<float, double>(g32, static_cast<double*>(grad), p->N * p->r, st));
+        return SOS_OK;
+    }
     SOS_CHECK(forward(p, prec, A, ws, st, nullptr));
     double* L = loss ? static_cast<double*>(loss) : at<double>(ws, w.loss);
     int32_t* status = at<int32_t>(ws, w.status);
@@ -179,6 +210,8 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
     if (o->optimizer == SOS_ADAM && (!s->m || !s->v)) return fail(SOS_E_INVALID, "sos_step: Adam needs m and v");
     if (o->optimizer != SOS_ADAM && o->optimizer != SOS_GD) return fail(SOS_E_INVALID, "sos_step: bad optimizer");
     if (o->flags & ~SOS_STEP_FP32_ADJOINT) return fail(SOS_E_INVALID, "sos_step: unknown flags");
+    if (o->slices != 0 && (o->slices < 2 || o->slices > kMaxSlices))
+        return fail(SOS_E_INVALID, "sos_step: slices must be 0 or 2..8");
     SOS_CHECK(ensure_device(p));
     cudaStream_t st = (cudaStream_t)stream;
     const Workspace w = workspace_layout(p, prec);
@@ -207,6 +240,18 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         SOS_CHECK(adj(p, h16, a16_cur, a16_next, static_cast<float*>(s->A), static_cast<float*>(s->m),
                       static_cast<float*>(s->v), o->optimizer, t, o->lr, o->beta1, o->beta2, o->eps, status, st));
         s->flags = SOS_STATE_BF16_CURRENT | (cur ? 0 : SOS_STATE_BF16_INDEX);
+        s->t = t;
+        return SOS_OK;
+    }
+    if (prec == SOS_FP64_TC) {
+        const int slices = o->slices == 0 ? kMaxSlices : o->slices;
+        float* g32 = at<float>(ws, w.grad);
+        SOS_CHECK(pass_tc64(p, static_cast<const double*>(s->A), static_cast<const double*>(pv), g32, loss, ws, st,
+                            slices));
+        SOS_CHECK(launch_update_mixed(p->N, p->r, static_cast<double*>(s->A), static_cast<double*>(s->m),
+                                      static_cast<double*>(s->v), g32, o->optimizer, t, o->lr, o->beta1, o->beta2,
+                                      o->eps, st));
+        s->flags = 0;
         s->t = t;
         return SOS_OK;
     }

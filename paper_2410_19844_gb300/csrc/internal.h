@@ -72,8 +72,14 @@ struct Workspace {
     size_t grad = 0;       // N x r gradient (float or double)
     size_t a16 = 0;        // 2 x N x ld16 bf16 copies of A, ping-pong (SOS_BF16 only)
     size_t h16 = 0;        // N x ld16h bf16 H(resid)   (SOS_BF16 only)
+    size_t resid32 = 0;    // M float residuals         (SOS_FP64_TC only)
+    size_t slices = 0;     // kMaxSlices x N x ld16 bf16 slices of A (SOS_FP64_TC only)
+    size_t ex = 0;         // N int32 row exponents     (SOS_FP64_TC only)
     size_t total = 0;
 };
+
+constexpr int kMaxSlices = 8;     // SOS_FP64_TC: 5-bit slices of A
+constexpr int kSliceBits = 5;
 
 // ---- plan ----------------------------------------------------------------
 
@@ -99,6 +105,9 @@ struct DeviceTables {
     // last one dehomogenised to 1); form_pairs[a] = (i, j), i <= j, of row a
     int32_t* form_rows = nullptr;
     int2* form_pairs = nullptr;
+    // every 256 x 256 tile of N x N (SOS_FP64_TC cross products), built on demand
+    int2* full_tiles2 = nullptr;
+    int num_full_tiles2 = 0;
 };
 
 }  // namespace sos
@@ -172,6 +181,17 @@ int launch_tc_adjoint_update_pair(const sos_plan_s* plan, const void* h16, const
 // into `grad` when it is not NULL; `ws` is a workspace of workspace_layout(plan, prec).
 int core_loss_grad(sos_plan_s* plan, int prec, const void* A, const void* p, void* grad, void* loss, void* ws,
                    cudaStream_t st, bool fp32_contraction);
+
+// ---- SOS_FP64_TC (slices.cu, kernels_tc2.cu) ----------------------------------------
+
+// c (FP64, zeroed here) = c(A) from `slices` 5-bit slices of A on tensor cores.
+int forward_tc64(sos_plan_s* plan, const double* A, void* ws, double* c, int slices, cudaStream_t st);
+// bf16 copy of an FP64 matrix (N x r into rows of ld16).
+int launch_cast_bf16_from_double(const double* A, int64_t N, int64_t r, void* a16, int64_t ld16, cudaStream_t st);
+int launch_tc_slices_pair(const sos_plan_s* plan, const void* si, const void* sj, bool cross, const int2* tiles,
+                          int num_tiles, const int32_t* ex, int shift, double* c, int32_t* status, cudaStream_t st);
+int launch_update_mixed(int64_t N, int64_t r, double* A, double* m, double* v, const float* grad, int optimizer,
+                        int64_t t, double lr, double b1, double b2, double eps, cudaStream_t st);
 
 // Whether the tensor-core contractions run on CTA pairs (environment variable
 // SOS_CTA_PAIRS = 0 or 1, read once; pairs by default).

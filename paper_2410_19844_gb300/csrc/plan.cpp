@@ -77,16 +77,23 @@ Workspace workspace_layout(const sos_plan_s* p, int prec) {
         off += (bytes + 255) / 256 * 256;
         return at;
     };
-    size_t elt = prec == SOS_FP64 ? 8 : 4;
+    const size_t elt = (prec == SOS_FP64 || prec == SOS_FP64_TC) ? 8 : 4;
     w.status = take(64 * sizeof(int32_t));
     w.partials = take(2 * kResidBlocks * sizeof(double));
     w.loss = take(2 * sizeof(double));
     w.c = take((size_t)p->M * elt);
     w.resid = take((size_t)p->M * elt);
-    w.grad = take((size_t)p->N * (size_t)p->r * elt);
+    w.grad = take((size_t)p->N * (size_t)p->r * (prec == SOS_FP64_TC ? 4 : elt));
     if (prec == SOS_BF16) {
         w.a16 = take(2 * (size_t)p->N * (size_t)p->ld16 * 2);
         w.h16 = take((size_t)p->N * (size_t)p->ld16h * 2);
+    }
+    if (prec == SOS_FP64_TC) {
+        w.a16 = take((size_t)p->N * (size_t)p->ld16 * 2);
+        w.h16 = take((size_t)p->N * (size_t)p->ld16h * 2);
+        w.resid32 = take((size_t)p->M * 4);
+        w.slices = take((size_t)kMaxSlices * p->N * (size_t)p->ld16 * 2);
+        w.ex = take((size_t)p->N * 4);
     }
     w.total = off;
     return w;
@@ -171,6 +178,7 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.pair_pos);
         cudaFree(p->dev.form_rows);
         cudaFree(p->dev.form_pairs);
+        cudaFree(p->dev.full_tiles2);
         if (cur >= 0) cudaSetDevice(cur);
     }
     delete p;
@@ -211,7 +219,7 @@ int sos_plan_idx(sos_plan_t p, int32_t* idx) {
 }
 
 int sos_workspace_size(sos_plan_t p, int prec, size_t* bytes) {
-    if (!p || !bytes || prec < SOS_BF16 || prec > SOS_FP64)
+    if (!p || !bytes || prec < SOS_BF16 || prec > SOS_FP64_TC)
         return fail(SOS_E_INVALID, "sos_workspace_size: bad argument");
     *bytes = workspace_layout(p, prec).total;
     return SOS_OK;

@@ -61,6 +61,7 @@ int sos_solve_opts_default(sos_solve_opts* o) {
     o->fp64_fp32_adjoint = 1;
     o->cert_tol = 1e-8;
     o->start_prec = SOS_BF16;
+    o->tc_fp64 = 0;
     return SOS_OK;
 }
 
@@ -139,6 +140,12 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
                 ++stall;
             }
             if (prec == SOS_BF16 && (rel < o->switch_rel || stall >= o->stall_checks)) {
+                if (o->tc_fp64) {                     // the FP64_TC stage follows instead
+                    out->rel_at_switch = rel;
+                    out->steps_bf16 = step;
+                    prec = SOS_FP64_TC;
+                    break;
+                }
                 nvtxMarkA("sos_solve: BF16 -> FP32");
                 out->rel_at_switch = rel;
                 out->steps_bf16 = step;
@@ -156,8 +163,66 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
         ++step;
     }
     if (prec == SOS_BF16) out->steps_bf16 = step;
-    out->steps_fp32 = step - out->steps_bf16;
+    out->steps_fp32 = prec == SOS_FP64_TC ? 0 : step - out->steps_bf16;
     out->min_rel = best;
+    if (prec == SOS_FP64_TC || (o->tc_fp64 && prec == SOS_BF16)) {
+        // ---- SOS_FP64_TC stage on an FP64 copy of the best BF16 point ----
+        nvtxMarkA("sos_solve: FP64_TC stage");
+        double *A64t = nullptr, *best64t = nullptr, *m64t = nullptr, *v64t = nullptr;
+        SOS_CHECK(mem.alloc(&A64t, NR));
+        SOS_CHECK(mem.alloc(&best64t, NR));
+        SOS_CHECK(mem.alloc(&m64t, NR));
+        SOS_CHECK(mem.alloc(&v64t, NR));
+        void* wst = nullptr;
+        SOS_CHECK(mem.alloc(reinterpret_cast<char**>(&wst), workspace_layout(p, SOS_FP64_TC).total));
+        SOS_CHECK(sos_workspace_init(p, SOS_FP64_TC, wst, stream));
+        SOS_CHECK(launch_convert<float, double>(best32, A64t, (int64_t)NR, st));
+        SOS_CHECK(launch_convert<float, double>(m32, m64t, (int64_t)NR, st));
+        SOS_CHECK(launch_convert<float, double>(v32, v64t, (int64_t)NR, st));
+        sos_state st64{A64t, m64t, v64t, s.t, 0, 0};
+        double best_t = INFINITY, gain = INFINITY;
+        int stall_t = 0, slices = kMaxSlices;
+        bool have = false;
+        for (int64_t k = 0; k <= o->fp64_steps; ++k) {
+            if (k % o->check_every == 0 || k == o->fp64_steps) {
+                // the loss of the previous step is at most check_every steps old; the
+                // check evaluates the current point at full slice accuracy
+                SOS_CHECK(sos_loss_grad(p, SOS_FP64_TC, A64t, p64, nullptr, loss, wst, stream));
+                SOS_CHECK(read_loss(loss, host, st));
+                if (!std::isfinite(host[0])) return fail(SOS_E_NONFINITE, "sos_solve: non-finite FP64_TC loss");
+                const double rel = rel_of(host[0]);
+                if (rel < best_t) {
+                    best_t = rel;
+                    have = true;
+                    SOS_CUDA(cudaMemcpyAsync(best64t, A64t, NR * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                }
+                if (rel < 0.99 * gain) {
+                    gain = rel;
+                    stall_t = 0;
+                } else {
+                    ++stall_t;
+                }
+                if (rel <= 0.5 * o->cert_tol || stall_t >= o->stall_checks || k == o->fp64_steps) break;
+                // slices for a forward about 2^-10 of the residual
+                const double bits = -std::log2(std::max(rel, 1e-300)) + 10.0;
+                slices = std::min(kMaxSlices, std::max(3, (int)std::ceil(bits / kSliceBits)));
+            }
+            sos_step_opts so{o->optimizer, o->lr_fp64, o->beta1, o->beta2, o->eps, 0, slices};
+            SOS_CHECK(sos_step(p, SOS_FP64_TC, &st64, p64, &so, nullptr, wst, stream));
+            ++out->steps_fp64;
+        }
+        out->min_rel_fp64 = best_t;
+        const double* final_A = have ? best64t : A64t;
+        double rel = 0.0;
+        int verdict = SOS_VERDICT_ERROR;
+        SOS_CHECK(sos_certify(p, final_A, 1, p64, o->cert_tol, &rel, &verdict, nullptr, stream));
+        SOS_CUDA(cudaMemcpyAsync(A, final_A, NR * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        SOS_CUDA(cudaStreamSynchronize(st));
+        out->steps = out->steps_bf16 + out->steps_fp32 + out->steps_fp64;
+        out->rel_resid_fp64 = rel;
+        out->verdict = verdict;
+        return SOS_OK;
+    }
 
     // ---- FP64 stage on an FP64 copy of the best FP32 point ----
     nvtxMarkA("sos_solve: FP64 stage");

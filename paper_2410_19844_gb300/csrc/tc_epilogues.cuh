@@ -59,6 +59,51 @@ struct SegmentSumEpilogue {
     }
 };
 
+// 2^e as a double (e in the normal range; outside it falls back to ldexp).
+__device__ __forceinline__ double pow2_int(int e) {
+    if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(1023 + e) << 52);
+    return ldexp(1.0, e);
+}
+
+// Forward of SOS_FP64_TC: acc is the product of two integer slices of A, exact
+// in FP32 (every partial sum is an integer below 2^24).  Scaled by
+// 2^(ex[a] + ex[b] + shift) it is an exact FP64 value, summed into the FP64
+// coefficients.  Diagonal units (slice i with itself) cover the upper triangle
+// with weights 1 (a = b) and 2 (a < b); cross units (slices i < j) cover every
+// ordered (a, b) with weight 2, which also counts the (j, i) unit.
+template <bool FULL>
+struct SliceSumEpilogue {
+    static constexpr const char* kName = FULL ? "tc_slices_cross" : "tc_slices_diag";
+    int N;
+    const int32_t* idx;
+    int64_t ld_idx;
+    double* c;
+    const int32_t* ex;
+    int shift;
+
+    __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
+        if (a0 >= N || b0 >= N) return;
+        if (!FULL && b0 + 31 < a0) return;
+        const int b = b0 + lane;
+        if (b >= N) return;
+        const int eb = ex[b] + shift;
+        const int32_t* col = idx + (int64_t)a0 * ld_idx + b;
+        int32_t g[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int a = a0 + i;
+            g[i] = (a < N && (FULL || a <= b)) ? __ldg(col + (int64_t)i * ld_idx) : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (g[i] >= 0) {
+                const double v = (double)stage[i * STAGE_LD + lane] * pow2_int(ex[a0 + i] + eb);
+                atomicAdd(c + g[i], (FULL || a0 + i != b) ? 2.0 * v : v);
+            }
+        }
+    }
+};
+
 // Adjoint / diagnostic GEMM: out[row][col] = scale * acc.
 struct StoreEpilogue {
     static constexpr const char* kName = "tc_adjoint";

@@ -8,7 +8,8 @@ import torch
 
 from . import _lib as L
 
-_DTYPE = {L.SOS_BF16: torch.float32, L.SOS_FP32: torch.float32, L.SOS_FP64: torch.float64}
+_DTYPE = {L.SOS_BF16: torch.float32, L.SOS_FP32: torch.float32, L.SOS_FP64: torch.float64,
+          L.SOS_FP64_TC: torch.float64}
 
 
 def _prec(prec) -> int:
@@ -80,8 +81,7 @@ class Plan:
     def coeffs(self, A: torch.Tensor, prec="fp32") -> torch.Tensor:
         prec = _prec(prec)
         self._check(A, prec)
-        c = torch.empty(self.M, dtype=torch.float64 if prec == L.SOS_FP64 else torch.float32,
-                        device=A.device)
+        c = torch.empty(self.M, dtype=_DTYPE[prec] if prec != L.SOS_BF16 else torch.float32, device=A.device)
         L.sos_coeffs(self.handle, prec, _ptr(A), _ptr(c), _ptr(self.workspace(prec, A.device)),
                      _stream_handle())
         return c
@@ -144,12 +144,12 @@ class Optimizer:
     through sos_step."""
 
     def __init__(self, plan: Plan, A: torch.Tensor, prec="bf16", optimizer="adam", lr=1e-2,
-                 beta1=0.9, beta2=0.999, eps=1e-8, fp32_adjoint=False):
+                 beta1=0.9, beta2=0.999, eps=1e-8, fp32_adjoint=False, slices=0):
         self.plan, self.prec = plan, _prec(prec)
         plan._check(A, self.prec)
         self.A = A
         self.opts = L.sos_step_opts(L.SOS_ADAM if optimizer == "adam" else L.SOS_GD, lr, beta1,
-                                    beta2, eps, L.SOS_STEP_FP32_ADJOINT if fp32_adjoint else 0)
+                                    beta2, eps, L.SOS_STEP_FP32_ADJOINT if fp32_adjoint else 0, slices)
         if optimizer == "adam":
             self.m, self.v = torch.zeros_like(A), torch.zeros_like(A)
         else:

@@ -8,7 +8,9 @@ are in bijection with the form's degree-2 monomials, so p = c(B) with B as the
 coefficient matrix (r = l, the paper's full-rank over-parameterisation).
 
 For each size: the target is built with the library's FP64 forward, A0 ~
-N(0, 0.1^2), sos_solve runs the BF16 -> FP32 -> FP64 ladder, and the report
+N(0, 0.1^2), and sos_solve runs in two modes: "classic" (BF16 -> FP32 -> FP64
+stages, the last two on CUDA cores) and "tc" (BF16 -> SOS_FP64_TC, the
+FP64-accurate forward on tensor cores from exact bf16 slices); the report
 lists steps, wall time and the FP64 certificate, next to the paper's time to
 solution (Sec. 3.1 table: Python/Jax + Adam on an i7-6500U laptop CPU; a
 different optimiser set-up and hardware, so context, not a like-for-like
@@ -16,7 +18,7 @@ comparison).  For n_form <= 30 the oracle recomputes the certificate of the
 returned A.  The last line fits time ~ n^k over n_form = 10..30 (the paper
 reports k ~ 4.5 for its method, Sec. 3.1).
 
-    python tests/report_paper_quartics.py [--sizes 10,15,20,25,30,100] [--out FILE]
+    python tests/report_paper_quartics.py [--sizes 10,15,20,25,30,100] [--modes classic,tc] [--out FILE]
 """
 import argparse
 import os
@@ -42,13 +44,18 @@ def main():
     ap.add_argument("--sizes", default="10,15,20,25,30,100")
     ap.add_argument("--out", default=None)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--modes", default="classic,tc",
+                    help="classic: BF16 -> FP32 -> FP64 stages; tc: BF16 -> SOS_FP64_TC stage")
     args = ap.parse_args()
+    modes = args.modes.split(",")
     sizes = [int(s) for s in args.sizes.split(",")]
     lines = ["# The paper's quartic forms (Sec. 3.1), solved by the precision ladder", "",
-             "| n (form) | N = l | M | steps bf16 / fp32 / fp64 | wall s | FP64 certificate | oracle check "
-             "| paper s (i7-6500U, Jax) |", "|---|---|---|---|---|---|---|---|"]
+             "classic: BF16 -> FP32 -> FP64 (FP32 adjoint) stages on CUDA cores after BF16; tc: BF16 -> SOS_FP64_TC "
+             "(FP64-accurate forward from exact bf16 slices on tensor cores, slices chosen from the residual).", "",
+             "| n (form) | N = l | M | mode | steps bf16 / fp32 / fp64 | wall s | FP64 certificate | oracle check "
+             "| paper s (i7-6500U, Jax) |", "|---|---|---|---|---|---|---|---|---|"]
     times = {}
-    for n_form in sizes:
+    for n_form, mode in [(nf, md) for nf in sizes for md in modes]:
         n = n_form - 1
         l = comb(n_form + 1, 2)
         pl = Plan(n, 4)
@@ -58,22 +65,24 @@ def main():
         A = torch.from_numpy(sos_inputs.normal_matrix(l, l, args.seed + 1, sigma=0.1)).cuda()
         torch.cuda.synchronize()
         t0 = time.time()
-        res = solve(pl, p64, A, max_steps=50000, check_every=50, fp64_steps=4000)
+        extra = {"tc_fp64": 1, "fp64_steps": 20000} if mode == "tc" else {"fp64_steps": 4000}
+        res = solve(pl, p64, A, max_steps=50000, check_every=50, **extra)
         dt = time.time() - t0
-        times[n_form] = dt
+        times[(n_form, mode)] = dt
         check = "-"
         if n_form <= 30:
             o = oracle.Oracle(n, 4)
             check = f"{o.certify(o.coeffs(A.cpu().numpy()), p64.cpu().numpy()):.3e}"
-        lines.append(f"| {n_form} | {l} | {pl.M} | {res['steps_bf16']} / {res['steps_fp32']} / {res['steps_fp64']} "
+        lines.append(f"| {n_form} | {l} | {pl.M} | {mode} | {res['steps_bf16']} / {res['steps_fp32']} / {res['steps_fp64']} "
                      f"| {dt:.2f} | {res['rel_resid_fp64']:.3e} ({'SOS' if res['verdict'] == 1 else 'not converged'}) "
                      f"| {check} | {PAPER_SECONDS.get(n_form, '-')} |")
         print(lines[-1], flush=True)
-    fit = [k for k in sorted(times) if k <= 30]
-    if len(fit) >= 3:
-        k, _ = np.polyfit(np.log(fit), np.log([times[x] for x in fit]), 1)
-        lines += ["", f"Fitted wall time ~ n^{k:.2f} over n = {fit[0]}..{fit[-1]} (the paper reports ~n^4.5 "
-                      f"for its method, Sec. 3.1)."]
+    for mode in modes:
+        fit = sorted(nf for (nf, md) in times if md == mode and nf <= 30)
+        if len(fit) >= 3:
+            k, _ = np.polyfit(np.log(fit), np.log([times[(x, mode)] for x in fit]), 1)
+            lines += ["", f"{mode}: fitted wall time ~ n^{k:.2f} over n = {fit[0]}..{fit[-1]} (the paper reports "
+                          f"~n^4.5 for its method, Sec. 3.1)."]
     text = "\n".join(lines) + "\n"
     print(text)
     if args.out:

@@ -114,3 +114,17 @@ def test_full_size_bf16_gd_step(full):
         want = A32[a].astype(np.float64) - lr * g
         tol = lr * bound + 2.0 ** -24 * (np.abs(want) + lr * np.abs(g)) + 1e-30
         assert np.all(np.abs(new_rows[i] - want) <= tol), f"row {a}"
+
+
+def test_full_size_fp64_tc_coefficients(full):
+    """SOS_FP64_TC at the benchmark's size (r = 10,626 <= 17,458, so every slice
+    product is exact): sampled coefficients within 10 2^-40 of the same sums
+    over the rows' power-of-two scales (8 slices; see test_gpu_fp64_tc.py)."""
+    o, pl, A32, _, cidx, _ = full
+    A64 = A32.astype(np.float64)
+    c = pl.coeffs(torch.from_numpy(A64).cuda(), "fp64_tc")[torch.from_numpy(cidx).cuda()].cpu().numpy()
+    c_ref, c_abs = _coeffs_ref(o, A64, cidx)
+    e = np.frexp(np.abs(A64).max(axis=1))[1].astype(np.float64)
+    E = np.repeat(np.exp2(e)[:, None], A64.shape[1], axis=1)
+    scale = np.array([o.coeff_at(E, int(g)) for g in cidx])
+    assert np.all(np.abs(c - c_ref) <= 10 * 2.0 ** -40 * scale + 1e-15 * c_abs)
