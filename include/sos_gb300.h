@@ -71,8 +71,10 @@ typedef enum {
  * the rows' scales for 8 slices.  The residual and loss are FP64; the adjoint
  * runs on tensor cores from bf16 H(r) and bf16 A (its error is proportional
  * to the residual, so iterations still converge to the exact fit); the update
- * is FP64.  Supported by sos_coeffs, sos_loss_grad (grad is double), sos_step
- * and sos_solve; other calls reject it with SOS_E_INVALID. */
+ * subtracts an FP32 step from the FP64 iterate, and the optimiser's moments m
+ * and v are FP32 arrays in this precision.  Supported by sos_coeffs,
+ * sos_loss_grad (grad is double), sos_step and sos_solve; other calls reject
+ * it with SOS_E_INVALID. */
 typedef enum { SOS_BF16 = 0, SOS_FP32 = 1, SOS_FP64 = 2, SOS_FP64_TC = 3 } sos_prec;
 typedef enum { SOS_ADAM = 0, SOS_GD = 1 } sos_opt;
 typedef enum {

@@ -39,7 +39,6 @@ int pass_tc64(sos_plan_s* p, const double* A, const double* pv, float* g32, void
     float* r32 = at<float>(ws, w.resid32);
     SOS_CHECK(launch_convert<double, float>(resid, r32, p->M, st));
     SOS_CHECK(launch_build_h16(p, r32, at<char>(ws, w.h16), st));
-    SOS_CHECK(launch_cast_bf16_from_double(A, p->N, p->r, at<char>(ws, w.a16), p->ld16, st));
     return launch_tc_adjoint_pair(p, at<char>(ws, w.h16), at<char>(ws, w.a16), g32, status, st);
 }
 
@@ -248,8 +247,8 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         float* g32 = at<float>(ws, w.grad);
         SOS_CHECK(pass_tc64(p, static_cast<const double*>(s->A), static_cast<const double*>(pv), g32, loss, ws, st,
                             slices));
-        SOS_CHECK(launch_update_mixed(p->N, p->r, static_cast<double*>(s->A), static_cast<double*>(s->m),
-                                      static_cast<double*>(s->v), g32, o->optimizer, t, o->lr, o->beta1, o->beta2,
+        SOS_CHECK(launch_update_mixed(p->N, p->r, static_cast<double*>(s->A), static_cast<float*>(s->m),
+                                      static_cast<float*>(s->v), g32, o->optimizer, t, o->lr, o->beta1, o->beta2,
                                       o->eps, st));
         s->flags = 0;
         s->t = t;

@@ -73,7 +73,7 @@ struct Workspace {
     size_t a16 = 0;        // 2 x N x ld16 bf16 copies of A, ping-pong (SOS_BF16 only)
     size_t h16 = 0;        // N x ld16h bf16 H(resid)   (SOS_BF16 only)
     size_t resid32 = 0;    // M float residuals         (SOS_FP64_TC only)
-    size_t slices = 0;     // kMaxSlices x N x ld16 bf16 slices of A (SOS_FP64_TC only)
+    size_t slices = 0;     // kMaxSlices x NP x ld16 bf16 slices of A, NP = N rounded up to 256 (SOS_FP64_TC)
     size_t ex = 0;         // N int32 row exponents     (SOS_FP64_TC only)
     size_t total = 0;
 };
@@ -105,9 +105,13 @@ struct DeviceTables {
     // last one dehomogenised to 1); form_pairs[a] = (i, j), i <= j, of row a
     int32_t* form_rows = nullptr;
     int2* form_pairs = nullptr;
-    // every 256 x 256 tile of N x N (SOS_FP64_TC cross products), built on demand
-    int2* full_tiles2 = nullptr;
-    int num_full_tiles2 = 0;
+    // SOS_FP64_TC, built on demand: the 256 x 256 tiles of every slice pair in
+    // the stacked coordinates, ordered by i + j; the pairs with i + j < s are
+    // the first slice_tile_count[s] entries
+    int2* slice_tiles2 = nullptr;
+    int slice_tile_count[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int slice_pairs = 0;                // pairs (i <= j) with i + j < kMaxSlices
+    int slice_pair_offset[37] = {0};    // tiles of the u-th pair: [offset[u], offset[u + 1])
 };
 
 }  // namespace sos
@@ -184,13 +188,14 @@ int core_loss_grad(sos_plan_s* plan, int prec, const void* A, const void* p, voi
 
 // ---- SOS_FP64_TC (slices.cu, kernels_tc2.cu) ----------------------------------------
 
-// c (FP64, zeroed here) = c(A) from `slices` 5-bit slices of A on tensor cores.
+// c (FP64, zeroed here) = c(A) from `slices` 5-bit slices of A on tensor cores;
+// also leaves the bf16 copy of A in the workspace's a16.
 int forward_tc64(sos_plan_s* plan, const double* A, void* ws, double* c, int slices, cudaStream_t st);
-// bf16 copy of an FP64 matrix (N x r into rows of ld16).
-int launch_cast_bf16_from_double(const double* A, int64_t N, int64_t r, void* a16, int64_t ld16, cudaStream_t st);
-int launch_tc_slices_pair(const sos_plan_s* plan, const void* si, const void* sj, bool cross, const int2* tiles,
-                          int num_tiles, const int32_t* ex, int shift, double* c, int32_t* status, cudaStream_t st);
-int launch_update_mixed(int64_t N, int64_t r, double* A, double* m, double* v, const float* grad, int optimizer,
+// Every slice pair of the stacked slices S (slice i in rows i * NP ..) listed in
+// `tiles` (stacked 256 x 256 tile coordinates), in one launch.
+int launch_tc_slices_pair(const sos_plan_s* plan, const void* S, int64_t NP, const int2* tiles, int num_tiles,
+                          const int32_t* ex, double* c, int32_t* status, cudaStream_t st);
+int launch_update_mixed(int64_t N, int64_t r, double* A, float* m, float* v, const float* grad, int optimizer,
                         int64_t t, double lr, double b1, double b2, double eps, cudaStream_t st);
 
 // Whether the tensor-core contractions run on CTA pairs (environment variable

@@ -340,19 +340,15 @@ int launch_tc_adjoint_pair(const sos_plan_s* p, const void* h16, const void* a16
                                   status, st);
 }
 
-int launch_tc_slices_pair(const sos_plan_s* p, const void* si, const void* sj, bool cross, const int2* tiles,
-                          int num_tiles, const int32_t* ex, int shift, double* c, int32_t* status, cudaStream_t st) {
+int launch_tc_slices_pair(const sos_plan_s* p, const void* S, int64_t NP, const int2* tiles, int num_tiles,
+                          const int32_t* ex, double* c, int32_t* status, cudaStream_t st) {
     using namespace tc2;
     CUtensorMap mA, mB;
-    SOS_CHECK(make_bf16_map(&mA, si, p->r, p->N, p->ld16, BK, BM));
-    SOS_CHECK(make_bf16_map(&mB, sj, p->r, p->N, p->ld16, BK, BN / 2));
-    const int nkb = (int)ceil_div(p->r, BK);
-    if (cross) {
-        tc::SliceSumEpilogue<true> epi{(int)p->N, p->dev.idx, p->ld_idx, c, ex, shift};
-        return launch_pair_gemm<false>(mA, mB, nkb, tiles, num_tiles, epi, status, st);
-    }
-    tc::SliceSumEpilogue<false> epi{(int)p->N, p->dev.idx, p->ld_idx, c, ex, shift};
-    return launch_pair_gemm<false>(mA, mB, nkb, tiles, num_tiles, epi, status, st);
+    const int64_t rows = (int64_t)kMaxSlices * NP;
+    SOS_CHECK(make_bf16_map(&mA, S, p->r, rows, p->ld16, BK, BM));
+    SOS_CHECK(make_bf16_map(&mB, S, p->r, rows, p->ld16, BK, BN / 2));
+    tc::SliceSumEpilogue epi{(int)p->N, (int)NP, p->dev.idx, p->ld_idx, c, ex};
+    return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), tiles, num_tiles, epi, status, st);
 }
 
 int diag_gemm_pair(int b_mn_major, const void* X, const void* Y, float* D, int64_t m, int64_t n, int64_t k,

@@ -92,7 +92,7 @@ Workspace workspace_layout(const sos_plan_s* p, int prec) {
         w.a16 = take((size_t)p->N * (size_t)p->ld16 * 2);
         w.h16 = take((size_t)p->N * (size_t)p->ld16h * 2);
         w.resid32 = take((size_t)p->M * 4);
-        w.slices = take((size_t)kMaxSlices * p->N * (size_t)p->ld16 * 2);
+        w.slices = take((size_t)kMaxSlices * (size_t)round_up(p->N, 256) * (size_t)p->ld16 * 2);
         w.ex = take((size_t)p->N * 4);
     }
     w.total = off;
@@ -178,7 +178,7 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.pair_pos);
         cudaFree(p->dev.form_rows);
         cudaFree(p->dev.form_pairs);
-        cudaFree(p->dev.full_tiles2);
+        cudaFree(p->dev.slice_tiles2);
         if (cur >= 0) cudaSetDevice(cur);
     }
     delete p;

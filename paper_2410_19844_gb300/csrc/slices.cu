@@ -31,69 +31,76 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// One block per row: the row's largest magnitude, then its digits.
+// One block per row: the row's largest magnitude, then its digits, computed on
+// the integer pipes from the bits of each double (FP64 arithmetic is slow on
+// this GPU): |x| = m 2^q with m the 53-bit significand, X = floor(|x| 2^(52 - e))
+// by a right shift of m, and digit i = bits 52 - 5 (i + 1) .. 52 - 5 i - 1 of X,
+// with the sign of x.  Also writes the bf16 copy of A that the adjoint reads.
 __global__ void __launch_bounds__(kThreads) split_rows_kernel(const double* __restrict__ A, int64_t N, int64_t r,
                                                               int slices, __nv_bfloat16* __restrict__ S,
                                                               int64_t slice_stride, int64_t ld16,
-                                                              int32_t* __restrict__ ex) {
-    __shared__ double red[kThreads / 32];
+                                                              int32_t* __restrict__ ex,
+                                                              __nv_bfloat16* __restrict__ a16) {
+    __shared__ unsigned long long red[kThreads / 32];
     const int64_t a = blockIdx.x;
     if (a >= N) return;
-    const double* row = A + a * r;
-    double mx = 0.0;
-    for (int64_t k = threadIdx.x; k < r; k += kThreads) mx = fmax(mx, fabs(row[k]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(A + a * r);
+    const unsigned long long kAbs = 0x7fffffffffffffffull;
+    unsigned long long mx = 0;      // largest |x| by its bits (monotone for non-negative doubles)
+    for (int64_t k = threadIdx.x; k < r; k += kThreads) mx = max(mx, row[k] & kAbs);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x < 32) {
-        mx = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mx = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (threadIdx.x == 0) red[0] = mx;
     }
     __syncthreads();
-    mx = red[0];
+    const double mxd = __longlong_as_double((long long)red[0]);
     int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);      // mx = f 2^e, f in [0.5, 1)
+    if (mxd > 0.0 && isfinite(mxd)) frexp(mxd, &e);     // mxd = f 2^e, f in [0.5, 1)
     if (threadIdx.x == 0) ex[a] = e;
-    const double scale = ldexp(1.0, -e);
     for (int64_t k = threadIdx.x; k < r; k += kThreads) {
-        double x = row[k] * scale;                        // |x| < 1, exact
+        const unsigned long long bits = row[k];
+        const int biased = (int)((bits >> 52) & 0x7ff);
+        const unsigned long long frac = bits & 0xfffffffffffffull;
+        // |x| = sig 2^(q), q = biased - 1075 (normal) or -1074 (subnormal)
+        const unsigned long long sig = biased ? (frac | (1ull << 52)) : frac;
+        const int q = biased ? biased - 1075 : -1074;
+        // X = sig 2^(q + 52 - e) < 2^52; for normal x, |x| < 2^e gives a right shift of at least 1
+        const int rshift = e - 52 - q;
+        const unsigned long long X = rshift >= 64 ? 0ull : rshift >= 0 ? (sig >> rshift) : (sig << (-rshift));
+        const bool neg = (bits >> 63) != 0;
+        const bool nonfinite = biased == 0x7ff;            // carried into the products as NaN
         for (int i = 0; i < slices; ++i) {
-            x *= 32.0;                                    // exact
-            const double d = trunc(x);
-            x -= d;                                       // exact
-            S[i * slice_stride + a * ld16 + k] = __double2bfloat16(d);   // |d| <= 31: exact
+            const int d = (int)((X >> (52 - kSliceBits * (i + 1))) & 31ull);
+            const float f = nonfinite ? __int_as_float(0x7fc00000) : (float)(neg ? -d : d);
+            S[i * slice_stride + a * ld16 + k] = __float2bfloat16_rn(f);   // exact for |d| <= 31
         }
+        a16[a * ld16 + k] = __float2bfloat16_rn((float)__longlong_as_double((long long)bits));
     }
 }
 
-__global__ void cast_bf16_from_double_kernel(const double* __restrict__ A, int64_t N, int64_t r,
-                                             __nv_bfloat16* __restrict__ a16, int64_t ld16) {
-    const int64_t total = N * r;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = i / r, col = i - row * r;
-        a16[row * ld16 + col] = __float2bfloat16_rn((float)A[i]);
-    }
-}
-
-__global__ void update_mixed_kernel(int64_t count, double* __restrict__ A, double* __restrict__ m,
-                                    double* __restrict__ v, const float* __restrict__ g, int optimizer, double lr,
-                                    double b1, double b2, double eps, double c1, double c2) {
+// FP64 iterate, FP32 gradient and FP32 moments: only the final subtraction (and
+// its conversion) runs on the FP64 pipe.
+__global__ void update_mixed_kernel(int64_t count, double* __restrict__ A, float* __restrict__ m,
+                                    float* __restrict__ v, const float* __restrict__ g, int optimizer, float lr,
+                                    float b1, float b2, float eps, float c1, float c2) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double gi = (double)g[i];
-        double a = A[i];
+        const float gi = g[i];
+        float step;
         if (optimizer == SOS_GD) {
-            a -= lr * gi;
+            step = lr * gi;
         } else {
-            const double mi = b1 * m[i] + (1.0 - b1) * gi;
-            const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+            const float mi = b1 * m[i] + (1.0f - b1) * gi;
+            const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
             m[i] = mi;
             v[i] = vi;
-            a -= lr * (mi / c1) / (sqrt(vi / c2) + eps);
+            step = lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         }
-        A[i] = a;
+        A[i] -= (double)step;
     }
 }
 
@@ -101,17 +108,31 @@ int grid_for(int64_t count) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((count + kThreads - 1) / kThreads, 152 * 16));
 }
 
-// Every 256 x 256 tile of N x N, in bands of 8 row blocks (rows fastest in a band).
-int ensure_full_tiles(sos_plan_s* p) {
+// The tiles of every slice pair (i <= j, i + j < kMaxSlices) in stacked
+// coordinates, ordered by i + j: upper-triangle tiles for i = j, all tiles for
+// i < j, each pair in bands of 8 row blocks (rows fastest in a band).
+int ensure_slice_tiles(sos_plan_s* p) {
     std::lock_guard<std::mutex> lock(p->mu);
-    if (p->dev.full_tiles2) return SOS_OK;
+    if (p->dev.slice_tiles2) return SOS_OK;
     const int TP = (int)ceil_div(p->N, 256), band = 8;
     std::vector<int2> t;
-    for (int i0 = 0; i0 < TP; i0 += band) {
-        const int i1 = std::min(TP, i0 + band);
-        for (int J = 0; J < TP; ++J)
-            for (int I = i0; I < i1; ++I) t.push_back(make_int2(I, J));
+    int count[kMaxSlices + 1] = {0};
+    int u = 0;
+    for (int o = 0; o < kMaxSlices; ++o) {
+        for (int i = 0; 2 * i <= o; ++i) {
+            const int j = o - i;
+            p->dev.slice_pair_offset[u++] = (int)t.size();
+            for (int i0 = 0; i0 < TP; i0 += band) {
+                const int i1 = std::min(TP, i0 + band);
+                for (int J = (i == j ? i0 : 0); J < TP; ++J)
+                    for (int I = i0; I < i1; ++I)
+                        if (i != j || J >= I) t.push_back(make_int2(i * TP + I, j * TP + J));
+            }
+        }
+        count[o + 1] = (int)t.size();
     }
+    p->dev.slice_pair_offset[u] = (int)t.size();
+    p->dev.slice_pairs = u;
     int2* d = nullptr;
     cudaError_t e = cudaMalloc(&d, t.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMemcpy(d, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice);
@@ -119,63 +140,62 @@ int ensure_full_tiles(sos_plan_s* p) {
         cudaFree(d);
         return cuda_fail(e, "SOS_FP64_TC: tile list");
     }
-    p->dev.full_tiles2 = d;
-    p->dev.num_full_tiles2 = (int)t.size();
+    p->dev.slice_tiles2 = d;
+    for (int s = 0; s <= kMaxSlices; ++s) p->dev.slice_tile_count[s] = count[s];
     return SOS_OK;
 }
 
 }  // namespace
 
-int launch_cast_bf16_from_double(const double* A, int64_t N, int64_t r, void* a16, int64_t ld16, cudaStream_t st) {
-    {
-        KernelScope ks_("cast_bf16", st);
-        cast_bf16_from_double_kernel<<<grid_for(N * r), kThreads, 0, st>>>(A, N, r, (__nv_bfloat16*)a16, ld16);
-    }
-    SOS_CUDA(cudaGetLastError());
-    return SOS_OK;
-}
-
-int launch_update_mixed(int64_t N, int64_t r, double* A, double* m, double* v, const float* grad, int optimizer,
+int launch_update_mixed(int64_t N, int64_t r, double* A, float* m, float* v, const float* grad, int optimizer,
                         int64_t t, double lr, double b1, double b2, double eps, cudaStream_t st) {
     const double c1 = 1.0 - std::pow(b1, (double)t), c2 = 1.0 - std::pow(b2, (double)t);
     {
         KernelScope ks_("update", st);
-        update_mixed_kernel<<<grid_for(N * r), kThreads, 0, st>>>(N * r, A, m, v, grad, optimizer, lr, b1, b2, eps,
-                                                                  c1, c2);
+        update_mixed_kernel<<<grid_for(N * r), kThreads, 0, st>>>(N * r, A, m, v, grad, optimizer, (float)lr,
+                                                                  (float)b1, (float)b2, (float)eps, (float)c1,
+                                                                  (float)c2);
     }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
 }
 
 int forward_tc64(sos_plan_s* p, const double* A, void* ws, double* c, int slices, cudaStream_t st) {
+    // the slices, the row exponents and the bf16 copy of A all come from one pass over A
     if (!use_cta_pairs()) return fail(SOS_E_UNSUPPORTED, "SOS_FP64_TC needs the CTA-pair kernels (SOS_CTA_PAIRS=1)");
     if (slices < 2 || slices > kMaxSlices) return fail(SOS_E_INVALID, "SOS_FP64_TC: slices must be 2..8");
     if (p->r * 31 * 31 >= (int64_t)1 << 24)
         return fail(SOS_E_UNSUPPORTED, "SOS_FP64_TC: r too large for exact slice products (r <= 17458)");
-    if (p->N > INT32_MAX / 2) return fail(SOS_E_UNSUPPORTED, "SOS_FP64_TC: N too large");
-    SOS_CHECK(ensure_full_tiles(p));
+    const int64_t NP = round_up(p->N, 256);
+    if ((int64_t)kMaxSlices * NP > INT32_MAX / 2) return fail(SOS_E_UNSUPPORTED, "SOS_FP64_TC: N too large");
+    SOS_CHECK(ensure_slice_tiles(p));
     const Workspace w = workspace_layout(p, SOS_FP64_TC);
     char* base = static_cast<char*>(ws);
     __nv_bfloat16* S = reinterpret_cast<__nv_bfloat16*>(base + w.slices);
     int32_t* ex = reinterpret_cast<int32_t*>(base + w.ex);
     int32_t* status = reinterpret_cast<int32_t*>(base + w.status);
-    const int64_t stride = p->N * p->ld16;
     SOS_CUDA(cudaMemsetAsync(c, 0, (size_t)p->M * sizeof(double), st));
     {
         KernelScope ks_("split_rows", st);
-        split_rows_kernel<<<(unsigned)p->N, kThreads, 0, st>>>(A, p->N, p->r, slices, S, stride, p->ld16, ex);
+        split_rows_kernel<<<(unsigned)p->N, kThreads, 0, st>>>(A, p->N, p->r, slices, S, NP * p->ld16, p->ld16, ex,
+                                                               reinterpret_cast<__nv_bfloat16*>(base + w.a16));
     }
     SOS_CUDA(cudaGetLastError());
-    // smallest terms first, so the FP64 sums add the large contributions last
-    for (int o = slices - 1; o >= 0; --o)          // o = i + j
-        for (int i = 0; 2 * i <= o; ++i) {
-            const int j = o - i;
-            const bool cross = i != j;
-            SOS_CHECK(launch_tc_slices_pair(p, S + i * stride, S + j * stride, cross,
-                                            cross ? p->dev.full_tiles2 : p->dev.fwd_tiles2,
-                                            cross ? p->dev.num_full_tiles2 : p->dev.num_fwd_tiles2, ex,
-                                            -kSliceBits * (o + 2), c, status, st));
-        }
+    // Every pair with i + j < slices.  Small plans run them all in one
+    // persistent launch (a pair alone would leave most of its last wave of
+    // CTA pairs idle); when one pair alone fills at least 8 waves, one launch
+    // per pair runs faster (measured at N = 10,626: 0.93 against 0.84 of the
+    // tensor peak).
+    const int64_t TP = ceil_div(p->N, 256);
+    const int64_t waves = TP * TP / std::max(1, p->dev.num_sms / 2);
+    const int total = p->dev.slice_tile_count[slices];
+    if (waves < 8)
+        return launch_tc_slices_pair(p, S, NP, p->dev.slice_tiles2, total, ex, c, status, st);
+    for (int u = 0; u < p->dev.slice_pairs && p->dev.slice_pair_offset[u] < total; ++u) {
+        const int off = p->dev.slice_pair_offset[u];
+        SOS_CHECK(launch_tc_slices_pair(p, S, NP, p->dev.slice_tiles2 + off, p->dev.slice_pair_offset[u + 1] - off,
+                                        ex, c, status, st));
+    }
     return SOS_OK;
 }
 

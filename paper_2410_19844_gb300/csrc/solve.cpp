@@ -168,18 +168,15 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
     if (prec == SOS_FP64_TC || (o->tc_fp64 && prec == SOS_BF16)) {
         // ---- SOS_FP64_TC stage on an FP64 copy of the best BF16 point ----
         nvtxMarkA("sos_solve: FP64_TC stage");
-        double *A64t = nullptr, *best64t = nullptr, *m64t = nullptr, *v64t = nullptr;
+        // the FP32 moments carry over as they are (SOS_FP64_TC keeps m, v in FP32)
+        double *A64t = nullptr, *best64t = nullptr;
         SOS_CHECK(mem.alloc(&A64t, NR));
         SOS_CHECK(mem.alloc(&best64t, NR));
-        SOS_CHECK(mem.alloc(&m64t, NR));
-        SOS_CHECK(mem.alloc(&v64t, NR));
         void* wst = nullptr;
         SOS_CHECK(mem.alloc(reinterpret_cast<char**>(&wst), workspace_layout(p, SOS_FP64_TC).total));
         SOS_CHECK(sos_workspace_init(p, SOS_FP64_TC, wst, stream));
         SOS_CHECK(launch_convert<float, double>(best32, A64t, (int64_t)NR, st));
-        SOS_CHECK(launch_convert<float, double>(m32, m64t, (int64_t)NR, st));
-        SOS_CHECK(launch_convert<float, double>(v32, v64t, (int64_t)NR, st));
-        sos_state st64{A64t, m64t, v64t, s.t, 0, 0};
+        sos_state st64{A64t, m32, v32, s.t, 0, 0};
         double best_t = INFINITY, gain = INFINITY;
         int stall_t = 0, slices = kMaxSlices;
         bool have = false;

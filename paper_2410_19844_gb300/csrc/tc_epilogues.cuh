@@ -65,40 +65,43 @@ __device__ __forceinline__ double pow2_int(int e) {
     return ldexp(1.0, e);
 }
 
-// Forward of SOS_FP64_TC: acc is the product of two integer slices of A, exact
-// in FP32 (every partial sum is an integer below 2^24).  Scaled by
-// 2^(ex[a] + ex[b] + shift) it is an exact FP64 value, summed into the FP64
-// coefficients.  Diagonal units (slice i with itself) cover the upper triangle
-// with weights 1 (a = b) and 2 (a < b); cross units (slices i < j) cover every
-// ordered (a, b) with weight 2, which also counts the (j, i) unit.
-template <bool FULL>
+// Forward of SOS_FP64_TC.  The slices of A are stacked (slice i in rows
+// i * NP .. i * NP + N - 1, NP a multiple of 256), so one launch runs every
+// slice pair: a tile at stacked rows (i * NP + a, j * NP + b) is the product of
+// slices i and j.  acc is that product, exact in FP32 (every partial sum is an
+// integer below 2^24); scaled by 2^(ex[a] + ex[b] - 5 (i + j + 2)) it is an
+// exact FP64 value, summed into the FP64 coefficients.  Diagonal pairs (i = j)
+// cover the upper triangle with weights 1 (a = b) and 2 (a < b); cross pairs
+// (i < j) cover every ordered (a, b) with weight 2, which also counts (j, i).
 struct SliceSumEpilogue {
-    static constexpr const char* kName = FULL ? "tc_slices_cross" : "tc_slices_diag";
-    int N;
+    static constexpr const char* kName = "tc_slices";
+    int N, NP;
     const int32_t* idx;
     int64_t ld_idx;
     double* c;
     const int32_t* ex;
-    int shift;
 
     __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
-        if (a0 >= N || b0 >= N) return;
-        if (!FULL && b0 + 31 < a0) return;
-        const int b = b0 + lane;
+        const int si = a0 / NP, sj = b0 / NP;
+        const int al = a0 - si * NP, bl = b0 - sj * NP;
+        if (al >= N || bl >= N) return;
+        const bool full = si != sj;
+        if (!full && bl + 31 < al) return;
+        const int b = bl + lane;
         if (b >= N) return;
-        const int eb = ex[b] + shift;
-        const int32_t* col = idx + (int64_t)a0 * ld_idx + b;
+        const int eb = ex[b] - 5 * (si + sj + 2);
+        const int32_t* col = idx + (int64_t)al * ld_idx + b;
         int32_t g[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-            const int a = a0 + i;
-            g[i] = (a < N && (FULL || a <= b)) ? __ldg(col + (int64_t)i * ld_idx) : -1;
+            const int a = al + i;
+            g[i] = (a < N && (full || a <= b)) ? __ldg(col + (int64_t)i * ld_idx) : -1;
         }
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (g[i] >= 0) {
-                const double v = (double)stage[i * STAGE_LD + lane] * pow2_int(ex[a0 + i] + eb);
-                atomicAdd(c + g[i], (FULL || a0 + i != b) ? 2.0 * v : v);
+                const double v = (double)stage[i * STAGE_LD + lane] * pow2_int(ex[al + i] + eb);
+                atomicAdd(c + g[i], (full || al + i != b) ? 2.0 * v : v);
             }
         }
     }

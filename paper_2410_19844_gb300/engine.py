@@ -151,7 +151,10 @@ class Optimizer:
         self.opts = L.sos_step_opts(L.SOS_ADAM if optimizer == "adam" else L.SOS_GD, lr, beta1,
                                     beta2, eps, L.SOS_STEP_FP32_ADJOINT if fp32_adjoint else 0, slices)
         if optimizer == "adam":
-            self.m, self.v = torch.zeros_like(A), torch.zeros_like(A)
+            # SOS_FP64_TC keeps the moments in FP32 next to the FP64 iterate
+            mdt = torch.float32 if self.prec == L.SOS_FP64_TC else A.dtype
+            self.m = torch.zeros_like(A, dtype=mdt)
+            self.v = torch.zeros_like(A, dtype=mdt)
         else:
             self.m = self.v = None
         self.state = L.sos_state(_ptr(A), _ptr(self.m), _ptr(self.v), 0)

@@ -13,7 +13,9 @@ stage evaluates, at that stage's iterate:
   * the oracle's loss and gradient (FP64, CPU),
 and prints their relative differences.  Then runs sos_solve from the same
 start in the ladder (start BF16) and in plain FP32 (start FP32) and compares
-steps, wall time and certificates.  Needs a GPU; prints a markdown report.
+steps, wall time and certificates, and from the BF16 start with the SOS_FP64_TC
+stage (the FP64-accurate forward on tensor cores) in place of the FP32 and FP64
+stages.  Needs a GPU; prints a markdown report.
 
     python tests/report_precision_ladder.py [--out profiles/precision_ladder_n10_2d10.md]
 """
@@ -143,13 +145,15 @@ def main():
     # sos_solve: ladder vs plain FP32
     lines += ["## sos_solve from the same start", "",
               "| start | verdict | steps bf16 / fp32 / fp64 | wall s | certificate |", "|---|---|---|---|---|"]
-    for start in ("bf16", "fp32"):
+    runs = [("bf16", "bf16", {"fp64_steps": 4000}), ("fp32", "fp32", {"fp64_steps": 4000}),
+            ("bf16, then SOS_FP64_TC", "bf16", {"tc_fp64": 1, "fp64_steps": 20000})]
+    for label, start, extra in runs:
         A_s = torch.from_numpy(A0.copy()).cuda()
         torch.cuda.synchronize()
         t = time.time()
-        res = solve(pl, p64, A_s, start_prec=start, max_steps=40000, check_every=args.check_every, fp64_steps=4000)
+        res = solve(pl, p64, A_s, start_prec=start, max_steps=40000, check_every=args.check_every, **extra)
         dt = time.time() - t
-        lines.append(f"| {start} | {'SOS' if res['verdict'] == 1 else 'not converged'} | {res['steps_bf16']} / "
+        lines.append(f"| {label} | {'SOS' if res['verdict'] == 1 else 'not converged'} | {res['steps_bf16']} / "
                      f"{res['steps_fp32']} / {res['steps_fp64']} | {dt:.2f} | {res['rel_resid_fp64']:.3e} |")
     text = "\n".join(lines) + "\n"
     print(text)

@@ -133,3 +133,13 @@ def test_fp64_tc_rejects_what_it_cannot_do_exactly():
         pl.coeffs(A, "fp64_tc")
     with pytest.raises(L.SOSError):
         L.sos_loss_grad_batched(pl.handle, L.SOS_FP64_TC, 1, 0, 0, 0, 0, 0, 0)
+
+
+def test_fp64_tc_nonfinite_entry_sets_status():
+    """A NaN in A reaches the coefficients (its slices carry NaN) and the status word."""
+    o, A, p = problem(4, 6, 35, spread=False)
+    A[2, 3] = np.nan
+    pl = Plan(4, 6, 35)
+    pl.loss_grad(torch.from_numpy(A).to(DEV), torch.from_numpy(p).to(DEV), "fp64_tc")
+    assert pl.status("fp64_tc") == L.SOS_E_NONFINITE
+    assert pl.status("fp64_tc") == L.SOS_OK
