@@ -302,12 +302,15 @@ typedef struct {
     double cert_tol;          /* certificate threshold (Sec. 3: about 1e-8) */
     int start_prec;           /* SOS_BF16 (the ladder), SOS_FP32 (no BF16
                                  stage) or SOS_FP64 (FP64 steps only) */
-    int tc_fp64;              /* 1: after the BF16 stage, SOS_FP64_TC steps take the
-                                 place of the FP32 and FP64 stages (up to fp64_steps,
-                                 or until stall_checks checks without a 1% gain),
-                                 with slices chosen from the current residual so the
-                                 forward stays about 2^-10 of it; the certificate is
-                                 still the CUDA-core FP64 evaluation */
+    int tc_fp64;              /* 1 (default): after the BF16 stage, SOS_FP64_TC steps
+                                 take the place of the FP32 and FP64 stages (up to
+                                 fp64_steps, or until stall_checks checks without a
+                                 1% gain), with slices chosen from the current
+                                 residual so the forward stays about 2^-10 of it;
+                                 the certificate is still the CUDA-core FP64
+                                 evaluation.  Plans with r > 17,458 (or with the
+                                 CTA-pair kernels switched off) take the CUDA-core
+                                 stages.  0: always the CUDA-core stages */
 } sos_solve_opts;
 
 typedef struct {
@@ -322,7 +325,8 @@ typedef struct {
 
 /* Defaults: Adam, lr 1e-2 in every stage, 20000 BF16+FP32 steps, checks
  * every 50, switch at 1e-3 or 4 stalled checks, 2000 FP64 steps with the
- * FP32 adjoint, tolerance 1e-8, start in BF16. */
+ * FP32 adjoint, tolerance 1e-8, start in BF16, the SOS_FP64_TC stage after
+ * BF16 (tc_fp64 = 1). */
 int sos_solve_opts_default(sos_solve_opts* opts);
 
 /* Minimises 1/2 ||c(A) - p||^2 from the start point A by the precision

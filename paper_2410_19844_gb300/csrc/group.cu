@@ -60,8 +60,8 @@ template <typename T>
 __global__ void __launch_bounds__(kT)
 group_forward(const int* __restrict__ counts, const Item* __restrict__ items, const Inst<T>* __restrict__ insts,
               const long long* __restrict__ step) {
-    __shared__ T As[16][64];
-    __shared__ T Bs[16][64];
+    __shared__ T As[16][65];      // padded: staged with k fastest across threads
+    __shared__ T Bs[16][65];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int n_items = counts[0];
     const long long now = *step;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kT)
 group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, int cap,
               const Inst<T>* __restrict__ insts, const long long* __restrict__ step, int optimizer, double b1,
               double b2, double eps) {
-    __shared__ Tc Hs[16][64];
+    __shared__ Tc Hs[16][65];     // padded: staged with b fastest across threads
     __shared__ Tc Bs[16][64];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int n_items = counts[2];

@@ -74,8 +74,8 @@ simt_forward_kernel(const Tin* __restrict__ A, int64_t N, int64_t r, const int32
     if (J < I) return;
     A += (int64_t)blockIdx.z * strideA;
     c += (int64_t)blockIdx.z * strideC;
-    __shared__ Tacc As[16][64];
-    __shared__ Tacc Bs[16][64];
+    __shared__ Tacc As[16][65];   // padded: staged with k fastest across threads
+    __shared__ Tacc Bs[16][65];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t row0 = (int64_t)I * 64, col0 = (int64_t)J * 64;
     Tacc acc[4][4];
@@ -254,7 +254,7 @@ simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const 
     A += (int64_t)blockIdx.z * strideA;
     grad += (int64_t)blockIdx.z * strideA;
     resid += (int64_t)blockIdx.z * strideR;
-    __shared__ Tc Hs[16][64];
+    __shared__ Tc Hs[16][65];     // padded: staged with b fastest across threads
     __shared__ Tc Bs[16][64];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t row0 = (int64_t)blockIdx.y * 64, col0 = (int64_t)blockIdx.x * 64;

@@ -61,7 +61,7 @@ int sos_solve_opts_default(sos_solve_opts* o) {
     o->fp64_fp32_adjoint = 1;
     o->cert_tol = 1e-8;
     o->start_prec = SOS_BF16;
-    o->tc_fp64 = 0;
+    o->tc_fp64 = 1;
     return SOS_OK;
 }
 
@@ -113,6 +113,9 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
     auto rel_of = [&](double l) { return std::sqrt(2.0 * std::max(l, 0.0) / pp); };
     out->rel_start_fp64 = rel_of(host[0]);
 
+    // the SOS_FP64_TC stage needs exact slice products (r 31^2 < 2^24) and the
+    // CTA-pair kernels; without them the CUDA-core stages run instead
+    const bool tc = o->tc_fp64 && p->r * 31 * 31 < ((int64_t)1 << 24) && use_cta_pairs();
     int prec = o->start_prec == SOS_FP64 ? SOS_FP32 : o->start_prec;
     sos_state s{A32, m32, v32, 0, 0, 0};
     double best = INFINITY, last_gain = INFINITY;
@@ -140,7 +143,7 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
                 ++stall;
             }
             if (prec == SOS_BF16 && (rel < o->switch_rel || stall >= o->stall_checks)) {
-                if (o->tc_fp64) {                     // the FP64_TC stage follows instead
+                if (tc) {                             // the FP64_TC stage follows instead
                     out->rel_at_switch = rel;
                     out->steps_bf16 = step;
                     prec = SOS_FP64_TC;
@@ -165,7 +168,7 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
     if (prec == SOS_BF16) out->steps_bf16 = step;
     out->steps_fp32 = prec == SOS_FP64_TC ? 0 : step - out->steps_bf16;
     out->min_rel = best;
-    if (prec == SOS_FP64_TC || (o->tc_fp64 && prec == SOS_BF16)) {
+    if (prec == SOS_FP64_TC || (tc && prec == SOS_BF16)) {
         // ---- SOS_FP64_TC stage on an FP64 copy of the best BF16 point ----
         nvtxMarkA("sos_solve: FP64_TC stage");
         // the FP32 moments carry over as they are (SOS_FP64_TC keeps m, v in FP32)

@@ -125,8 +125,9 @@ class Plan:
 
 
 def solve(plan: Plan, p64: torch.Tensor, A: torch.Tensor, **opts) -> dict:
-    """Runs sos_solve (the BF16 -> FP32 -> FP64 ladder) on A (float64, in place);
-    keyword arguments override fields of the default options."""
+    """Runs sos_solve on A (float64, in place): BF16 steps, then SOS_FP64_TC
+    steps (or, with tc_fp64=0, FP32 then FP64 CUDA-core steps), then the FP64
+    certificate; keyword arguments override fields of the default options."""
     if A.dtype != torch.float64 or p64.dtype != torch.float64:
         raise ValueError("A and p must be float64 device tensors")
     o = L.sos_solve_opts_default()

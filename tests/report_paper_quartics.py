@@ -65,7 +65,7 @@ def main():
         A = torch.from_numpy(sos_inputs.normal_matrix(l, l, args.seed + 1, sigma=0.1)).cuda()
         torch.cuda.synchronize()
         t0 = time.time()
-        extra = {"tc_fp64": 1, "fp64_steps": 20000} if mode == "tc" else {"fp64_steps": 4000}
+        extra = {"tc_fp64": 1, "fp64_steps": 20000} if mode == "tc" else {"tc_fp64": 0, "fp64_steps": 4000}
         res = solve(pl, p64, A, max_steps=50000, check_every=50, **extra)
         dt = time.time() - t0
         times[(n_form, mode)] = dt

@@ -145,7 +145,7 @@ def main():
     # sos_solve: ladder vs plain FP32
     lines += ["## sos_solve from the same start", "",
               "| start | verdict | steps bf16 / fp32 / fp64 | wall s | certificate |", "|---|---|---|---|---|"]
-    runs = [("bf16", "bf16", {"fp64_steps": 4000}), ("fp32", "fp32", {"fp64_steps": 4000}),
+    runs = [("bf16", "bf16", {"tc_fp64": 0, "fp64_steps": 4000}), ("fp32", "fp32", {"tc_fp64": 0, "fp64_steps": 4000}),
             ("bf16, then SOS_FP64_TC", "bf16", {"tc_fp64": 1, "fp64_steps": 20000})]
     for label, start, extra in runs:
         A_s = torch.from_numpy(A0.copy()).cuda()
