@@ -121,6 +121,78 @@ simt_forward_kernel(const Tin* __restrict__ A, int64_t N, int64_t r, const int32
     }
 }
 
+// ---- the same with 128 x 128 tiles, for large plans ----------------------------------
+// 256 threads, 8 x 8 outputs each (rows ty + 16 u, columns tx + 16 v), K in
+// slices of 8 staged in shared memory (padded against bank conflicts); the next
+// slice is read from global memory into registers while the current one is
+// multiplied.  64 multiply-adds per 16 shared-memory loads.
+
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(kThreads)
+simt_forward128_kernel(const Tin* __restrict__ A, int64_t N, int64_t r, const int32_t* __restrict__ idx,
+                       int64_t ld_idx, Tacc* __restrict__ c, int64_t strideA, int64_t strideC) {
+    const int I = blockIdx.y, J = blockIdx.x;
+    if (J < I) return;
+    A += (int64_t)blockIdx.z * strideA;
+    c += (int64_t)blockIdx.z * strideC;
+    __shared__ Tacc As[8][129];
+    __shared__ Tacc Bs[8][129];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)I * 128, col0 = (int64_t)J * 128;
+    Tacc ra[4], rb[4];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = tid + kThreads * e, rr = q >> 3, kk = q & 7;
+            const int64_t gk = k0 + kk, ga = row0 + rr, gb = col0 + rr;
+            ra[e] = (ga < N && gk < r) ? (Tacc)A[ga * r + gk] : Tacc(0);
+            rb[e] = (gb < N && gk < r) ? (Tacc)A[gb * r + gk] : Tacc(0);
+        }
+    };
+    Tacc acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = Tacc(0);
+    fetch(0);
+    for (int64_t k0 = 0; k0 < r; k0 += 8) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = tid + kThreads * e;
+            As[q & 7][q >> 3] = ra[e];
+            Bs[q & 7][q >> 3] = rb[e];
+        }
+        __syncthreads();
+        if (k0 + 8 < r) fetch(k0 + 8);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            Tacc a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t a = row0 + ty + 16 * i;
+        if (a >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t b = col0 + tx + 16 * j;
+            if (b < N && b >= a) {
+                const Tacc w = (b == a) ? Tacc(1) : Tacc(2);
+                atomicAdd(&c[idx[a * ld_idx + b]], w * acc[i][j]);
+            }
+        }
+    }
+}
+
 // ---- residual and loss ----------------------------------------------------------
 // grid.y = instance.  With one block per instance the block reduces alone;
 // with several, the last block to finish (ticket counter) sums the per-block
@@ -305,6 +377,78 @@ simt_adjoint_kernel(const T* __restrict__ A, const T* __restrict__ resid, const 
     }
 }
 
+// 128 x 128 output tiles (rows a, columns k) for large plans; the contraction
+// over b in slices of 8, H gathered from the residual while staging.
+template <typename T, typename Tc>
+__global__ void __launch_bounds__(kThreads)
+simt_adjoint128_kernel(const T* __restrict__ A, const T* __restrict__ resid, const int32_t* __restrict__ idx,
+                       int64_t ld_idx, int64_t N, int64_t r, T* __restrict__ grad, int64_t strideA,
+                       int64_t strideR) {
+    A += (int64_t)blockIdx.z * strideA;
+    grad += (int64_t)blockIdx.z * strideA;
+    resid += (int64_t)blockIdx.z * strideR;
+    __shared__ Tc Hs[8][129];
+    __shared__ Tc Bs[8][129];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.y * 128, col0 = (int64_t)blockIdx.x * 128;
+    Tc rh[4], rb[4];
+    auto fetch = [&](int64_t b0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = tid + kThreads * e;
+            {   // H: 128 rows a x 8 columns b (b fastest: index rows are contiguous in b)
+                const int rr = q >> 3, kk = q & 7;
+                const int64_t a = row0 + rr, b = b0 + kk;
+                rh[e] = (a < N && b < N) ? (Tc)resid[idx[a * ld_idx + b]] : Tc(0);
+            }
+            {   // A: 8 rows b x 128 columns k (k fastest)
+                const int kk = q >> 7, cc = q & 127;
+                const int64_t b = b0 + kk, k = col0 + cc;
+                rb[e] = (b < N && k < r) ? (Tc)A[b * r + k] : Tc(0);
+            }
+        }
+    };
+    Tc acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = Tc(0);
+    fetch(0);
+    for (int64_t b0 = 0; b0 < N; b0 += 8) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = tid + kThreads * e;
+            Hs[q & 7][q >> 3] = rh[e];
+            Bs[q >> 7][q & 127] = rb[e];
+        }
+        __syncthreads();
+        if (b0 + 8 < N) fetch(b0 + 8);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            Tc a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = Hs[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t a = row0 + ty + 16 * i;
+        if (a >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t k = col0 + tx + 16 * j;
+            if (k < r) grad[a * r + k] = T(2) * (T)acc[i][j];
+        }
+    }
+}
+
 // ---- H(r) in bf16 for the tensor-core adjoint ----------------------------------------
 // H is symmetric (idx(a, b) = idx(b, a)), so each block reads the index table
 // and gathers the residual for one 64 x 64 tile on or above the diagonal and
@@ -452,12 +596,27 @@ int launch_cast_bf16(const float* A, int64_t N, int64_t r, void* a16, int64_t ld
     return SOS_OK;
 }
 
+// 128 x 128 tiles once a single problem fills a wave of them on 152 SMs
+// (N >= about 2100); 64 x 64 tiles otherwise.
+static bool use_simt128(int64_t N, int64_t batch) {
+    const int64_t t128 = ceil_div(N, 128);
+    return batch == 1 && t128 * (t128 + 1) / 2 >= 152;
+}
+
 template <typename Tin, typename Tacc>
 int launch_simt_forward(const sos_plan_s* p, const Tin* A, Tacc* c, int64_t batch, cudaStream_t st) {
-    const int64_t T = ceil_div(p->N, 64);
-    if (T > 65535 || batch > 65535) return fail(SOS_E_UNSUPPORTED, "simt_forward: too many tiles");
-    dim3 grid((unsigned)T, (unsigned)T, (unsigned)batch);
-    {
+    if (batch > 65535) return fail(SOS_E_UNSUPPORTED, "simt_forward: batch too large");
+    if (use_simt128(p->N, batch)) {
+        const int64_t T = ceil_div(p->N, 128);
+        if (T > 65535) return fail(SOS_E_UNSUPPORTED, "simt_forward: too many tiles");
+        dim3 grid((unsigned)T, (unsigned)T, (unsigned)batch);
+        KernelScope ks_("simt_forward", st);
+        simt_forward128_kernel<Tin, Tacc><<<grid, kThreads, 0, st>>>(A, p->N, p->r, p->dev.idx, p->ld_idx, c,
+                                                                     p->N * p->r, p->M);
+    } else {
+        const int64_t T = ceil_div(p->N, 64);
+        if (T > 65535) return fail(SOS_E_UNSUPPORTED, "simt_forward: too many tiles");
+        dim3 grid((unsigned)T, (unsigned)T, (unsigned)batch);
         KernelScope ks_("simt_forward", st);
         simt_forward_kernel<Tin, Tacc><<<grid, kThreads, 0, st>>>(A, p->N, p->r, p->dev.idx, p->ld_idx, c,
                                                                   p->N * p->r, p->M);
@@ -484,6 +643,21 @@ int launch_residual(const sos_plan_s* p, const T* c, const T* pv, T* resid, doub
 template <typename T>
 int launch_simt_adjoint(const sos_plan_s* p, const T* A, const T* resid, T* grad, int64_t batch, cudaStream_t st,
                         bool fp32_contraction) {
+    if (use_simt128(p->N, batch)) {
+        const int64_t TI = ceil_div(p->N, 128), TK = ceil_div(p->r, 128);
+        if (TI > 65535 || batch > 65535 || TK > INT32_MAX)
+            return fail(SOS_E_UNSUPPORTED, "simt_adjoint: too many tiles");
+        dim3 grid((unsigned)TK, (unsigned)TI, (unsigned)batch);
+        KernelScope ks_(fp32_contraction ? "simt_adjoint_fp32c" : "simt_adjoint", st);
+        if (fp32_contraction)
+            simt_adjoint128_kernel<T, float><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r,
+                                                                        grad, p->N * p->r, p->M);
+        else
+            simt_adjoint128_kernel<T, T><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r,
+                                                                    grad, p->N * p->r, p->M);
+        SOS_CUDA(cudaGetLastError());
+        return SOS_OK;
+    }
     const int64_t TI = ceil_div(p->N, 64), TK = ceil_div(p->r, 64);
     if (TI > 65535 || batch > 65535 || TK > INT32_MAX) return fail(SOS_E_UNSUPPORTED, "simt_adjoint: too many tiles");
     dim3 grid((unsigned)TK, (unsigned)TI, (unsigned)batch);

@@ -27,12 +27,15 @@
 namespace sos {
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 16;
+constexpr int kBM = 128, kBN = 128, kBK = 8;
 
 // C = A B with A(i, l) = A[i * as0 + l * as1] and B(l, j) = B[l * bs0 + j * bs1];
-// grid (ceil(Ncol / 64), ceil(M / 64), splits).  Split z covers l in
+// grid (ceil(Ncol / 128), ceil(M / 128), splits).  Split z covers l in
 // [z * kchunk, (z + 1) * kchunk) and writes its own M x Ncol block of C (at
 // C + z * split_stride), summed afterwards by split_sum_kernel in a fixed order.
+// 256 threads, 8 x 8 outputs each (rows ty + 16 u, columns tx + 16 v): 64
+// multiply-adds per 16 shared-memory loads.  The next K-slice is read from
+// global memory into registers while the current one is multiplied.
 template <typename T>
 __global__ void __launch_bounds__(256) strided_gemm_kernel(int64_t M, int64_t Ncol, int64_t K, int64_t kchunk,
                                                            const T* __restrict__ A, int64_t as0, int64_t as1,
@@ -44,59 +47,80 @@ __global__ void __launch_bounds__(256) strided_gemm_kernel(int64_t M, int64_t Nc
     const int64_t i0 = (int64_t)blockIdx.y * kBM, j0 = (int64_t)blockIdx.x * kBN;
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
     const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
-    T acc[4][4];
+    // staging map: element q = threadIdx.x + 256 e (e < 4) of each 128 x 8 slice,
+    // walking the operand's contiguous dimension fastest
+    T ra[4], rb[4];
+    auto fetch = [&](int64_t k0) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    for (int64_t k0 = kbeg; k0 < kend; k0 += kBK) {
-        // stage both tiles, walking the operand's contiguous dimension fastest
-        for (int e = threadIdx.x; e < kBM * kBK; e += 256) {
+        for (int e = 0; e < 4; ++e) {
+            const int q = threadIdx.x + 256 * e;
             int ii, kk;
             if (as1 == 1) {
-                ii = e / kBK;
-                kk = e % kBK;
+                ii = q / kBK;
+                kk = q % kBK;
             } else {
-                kk = e / kBM;
-                ii = e % kBM;
+                kk = q / kBM;
+                ii = q % kBM;
             }
             const int64_t gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < M && gk < kend) ? A[gi * as0 + gk * as1] : T(0);
-        }
-        for (int e = threadIdx.x; e < kBN * kBK; e += 256) {
-            int jj, kk;
+            ra[e] = (gi < M && gk < kend) ? A[gi * as0 + gk * as1] : T(0);
+            int jj;
             if (bs1 == 1) {
-                kk = e / kBN;
-                jj = e % kBN;
+                kk = q / kBN;
+                jj = q % kBN;
             } else {
-                jj = e / kBK;
-                kk = e % kBK;
+                jj = q / kBK;
+                kk = q % kBK;
             }
-            const int64_t gj = j0 + jj, gk = k0 + kk;
-            Bs[kk][jj] = (gj < Ncol && gk < kend) ? B[gk * bs0 + gj * bs1] : T(0);
+            const int64_t gj = j0 + jj, gk2 = k0 + kk;
+            rb[e] = (gj < Ncol && gk2 < kend) ? B[gk2 * bs0 + gj * bs1] : T(0);
         }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = threadIdx.x + 256 * e;
+            if (as1 == 1)
+                As[q % kBK][q / kBK] = ra[e];
+            else
+                As[q / kBM][q % kBM] = ra[e];
+            if (bs1 == 1)
+                Bs[q / kBN][q % kBN] = rb[e];
+            else
+                Bs[q % kBK][q / kBK] = rb[e];
+        }
+    };
+    T acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = T(0);
+    if (kbeg < kend) fetch(kbeg);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kBK) {
+        stash();
         __syncthreads();
+        if (k0 + kBK < kend) fetch(k0 + kBK);     // in flight during the products below
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
-            T a[4], b[4];
+            T a[8], b[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+            for (int u = 0; u < 8; ++u) a[u] = As[kk][ty + 16 * u];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
+            for (int v = 0; v < 8; ++v) b[v] = Bs[kk][tx + 16 * v];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+                for (int v = 0; v < 8; ++v) acc[u][v] += a[u] * b[v];
         }
         __syncthreads();
     }
     T* Cz = C + (int64_t)blockIdx.z * split_stride;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
         const int64_t i = i0 + ty + 16 * u;
         if (i >= M) continue;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < 8; ++v) {
             const int64_t j = j0 + tx + 16 * v;
             if (j < Ncol) Cz[i * ldc + j] = acc[u][v];
         }

@@ -202,6 +202,28 @@ def test_step_fp64_matches_oracle(optimizer):
         assert rel(A_dev.cpu().numpy(), Aref) < 1e-12
 
 
+# -- the 128 x 128 CUDA-core tiles (N >= about 2100) --------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_large_simt_tiles(prec):
+    """n = 13, 2d = 8: N = 2380 takes the 128 x 128 SIMT kernels (r = 300 keeps
+    the oracle quick; the tile grid depends on N only)."""
+    o, A, p = problem(13, 8, 300, squares=3)
+    pl = Plan(13, 8, 300)
+    dt = np.float64 if prec == "fp64" else np.float32
+    A_ = A.astype(dt)
+    p_ = p.astype(dt)
+    loss, _, g = pl.loss_grad(torch.from_numpy(A_).to(DEV), torch.from_numpy(p_).to(DEV), prec)
+    loss_ref, g_ref, _ = o.loss_grad(A_.astype(np.float64), p_.astype(np.float64))
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert abs(loss.item() - loss_ref) <= tol * loss_ref
+    assert rel(g.cpu().numpy(), g_ref) < tol
+    if prec == "fp32":    # the certificate's forward: FP32 A, FP64 sums
+        rel_c, _ = pl.certify(torch.from_numpy(A_).to(DEV), torch.from_numpy(p).to(DEV))
+        c = o.coeffs(A_.astype(np.float64))
+        assert abs(rel_c - o.certify(c, p)) <= 1e-10 * o.certify(c, p)
+
+
 # -- degenerate shapes -------------------------------------------------------------------
 
 DEGENERATE = [(1, 2, 1),      # one variable, quadratic, one square: N = 2, M = 3
