@@ -81,6 +81,15 @@ struct Workspace {
 constexpr int kMaxSlices = 8;     // SOS_FP64_TC: 5-bit slices of A
 constexpr int kSliceBits = 5;
 
+// SOS_FP64_TC with r 31^2 k < 2^24 (k >= 2): slice products of one order summed
+// in one accumulator, as the segments sa[s] x sb[s] of one product (symmetric:
+// (i, i) alone or (i, j) with (j, i)).
+constexpr int kMaxGroupSeg = 8;
+struct SliceGroup {
+    int nseg, order;
+    int sa[kMaxGroupSeg], sb[kMaxGroupSeg];
+};
+
 // ---- plan ----------------------------------------------------------------
 
 struct DeviceTables {
@@ -112,6 +121,10 @@ struct DeviceTables {
     int slice_tile_count[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int slice_pairs = 0;                // pairs (i <= j) with i + j < kMaxSlices
     int slice_pair_offset[37] = {0};    // tiles of the u-th pair: [offset[u], offset[u + 1])
+    // grouped form (r 31^2 2 < 2^24): groups by order, tiles (g * TP + I, J)
+    // with J >= I; groups of order < s own the first slice_tile_count[s] tiles
+    SliceGroup* slice_groups = nullptr;
+    bool slice_grouped = false;
 };
 
 }  // namespace sos
@@ -195,6 +208,9 @@ int forward_tc64(sos_plan_s* plan, const double* A, void* ws, double* c, int sli
 // `tiles` (stacked 256 x 256 tile coordinates), in one launch.
 int launch_tc_slices_pair(const sos_plan_s* plan, const void* S, int64_t NP, const int2* tiles, int num_tiles,
                           const int32_t* ex, double* c, int32_t* status, cudaStream_t st);
+// The grouped form: `groups` is a device array of SliceGroup.
+int launch_tc_slice_groups_pair(const sos_plan_s* plan, const void* S, int64_t NP, const int2* tiles, int num_tiles,
+                                const void* groups, const int32_t* ex, double* c, int32_t* status, cudaStream_t st);
 int launch_update_mixed(int64_t N, int64_t r, double* A, float* m, float* v, const float* grad, int optimizer,
                         int64_t t, double lr, double b1, double b2, double eps, cudaStream_t st);
 

@@ -59,6 +59,7 @@ template <bool B_MN_MAJOR, class Epilogue>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int nkb,
                     const int2* __restrict__ tiles, int num_tiles, Epilogue epi, int32_t* __restrict__ status) {
+    static_assert(!(Epilogue::kSegmented && B_MN_MAJOR), "segmented K runs with K-major operands only");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* base = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -112,7 +113,9 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             const int2 tile = tiles[t];
             const int arow = tile.x * PAIR_M + (int)rank * BM;
             const int bcol = tile.y * BN + (int)rank * (BN / 2);
-            for (int kb = 0; kb < nkb; kb += KATOMS) {
+            int nkbt = nkb;       // K blocks of this tile (all its segments)
+            if constexpr (Epilogue::kSegmented) nkbt = epi.segments(tile) * nkb;
+            for (int kb = 0; kb < nkbt; kb += KATOMS) {
                 if (*err || !mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT_NS)) {
                     ok = false;
                     break;
@@ -121,15 +124,25 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 const uint32_t bar = mapa_shared(smem_u32(&full[s]), 0);
 #pragma unroll
                 for (int at = 0; at < KATOMS; ++at) {
-                    const int kx = (kb + at) * BK;      // beyond K: zero fill, still counted
-                    tma_load_2d_pair(sA + s * A_BYTES + at * ATOM_A, &mapA, bar, kx, arow);
+                    int kx = (kb + at) * BK;            // beyond K: zero fill, still counted
+                    int ar = arow, bc = bcol;
+                    if constexpr (Epilogue::kSegmented) {
+                        // atom q of the tile: K block q % nkb of segment q / nkb; past the
+                        // last segment, a block beyond K (zero fill)
+                        const int q = kb + at;
+                        const int seg = q < nkbt ? q / nkb : 0;
+                        kx = q < nkbt ? (q - seg * nkb) * BK : nkb * BK;
+                        ar = epi.seg_arow(tile, seg) + (int)rank * BM;
+                        bc = epi.seg_brow(tile, seg) + (int)rank * (BN / 2);
+                    }
+                    tma_load_2d_pair(sA + s * A_BYTES + at * ATOM_A, &mapA, bar, kx, ar);
                     if (B_MN_MAJOR) {
 #pragma unroll
                         for (int j = 0; j < BN / 2 / 64; ++j)
                             tma_load_2d_pair(sB + s * B_BYTES + at * ATOM_B + j * (64 * BK * 2), &mapB, bar,
                                              bcol + 64 * j, kx);
                     } else {
-                        tma_load_2d_pair(sB + s * B_BYTES + at * ATOM_B, &mapB, bar, kx, bcol);
+                        tma_load_2d_pair(sB + s * B_BYTES + at * ATOM_B, &mapB, bar, kx, bc);
                     }
                 }
                 ++issued;
@@ -163,7 +176,9 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             }
             tc_fence_after();
             const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
-            for (int kb = 0; kb < nkb; kb += KATOMS) {
+            int nkbt = nkb;
+            if constexpr (Epilogue::kSegmented) nkbt = epi.segments(tiles[t]) * nkb;
+            for (int kb = 0; kb < nkbt; kb += KATOMS) {
                 if (*err || !mbar_wait(&full[s], ph, WAIT_LIMIT_NS)) {
                     ok = false;
                     break;
@@ -348,6 +363,18 @@ int launch_tc_slices_pair(const sos_plan_s* p, const void* S, int64_t NP, const 
     SOS_CHECK(make_bf16_map(&mA, S, p->r, rows, p->ld16, BK, BM));
     SOS_CHECK(make_bf16_map(&mB, S, p->r, rows, p->ld16, BK, BN / 2));
     tc::SliceSumEpilogue epi{(int)p->N, (int)NP, p->dev.idx, p->ld_idx, c, ex};
+    return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), tiles, num_tiles, epi, status, st);
+}
+
+int launch_tc_slice_groups_pair(const sos_plan_s* p, const void* S, int64_t NP, const int2* tiles, int num_tiles,
+                                const void* groups, const int32_t* ex, double* c, int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    CUtensorMap mA, mB;
+    const int64_t rows = (int64_t)kMaxSlices * NP;
+    SOS_CHECK(make_bf16_map(&mA, S, p->r, rows, p->ld16, BK, BM));
+    SOS_CHECK(make_bf16_map(&mB, S, p->r, rows, p->ld16, BK, BN / 2));
+    tc::SliceGroupEpilogue epi{(int)p->N, (int)NP, (int)(NP / 256), p->dev.idx, p->ld_idx, c, ex,
+                               static_cast<const SliceGroup*>(groups)};
     return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), tiles, num_tiles, epi, status, st);
 }
 

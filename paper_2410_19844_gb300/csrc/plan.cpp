@@ -179,6 +179,7 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.form_rows);
         cudaFree(p->dev.form_pairs);
         cudaFree(p->dev.slice_tiles2);
+        cudaFree(p->dev.slice_groups);
         if (cur >= 0) cudaSetDevice(cur);
     }
     delete p;

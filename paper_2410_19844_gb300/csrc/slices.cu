@@ -108,25 +108,71 @@ int grid_for(int64_t count) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((count + kThreads - 1) / kThreads, 152 * 16));
 }
 
-// The tiles of every slice pair (i <= j, i + j < kMaxSlices) in stacked
-// coordinates, ordered by i + j: upper-triangle tiles for i = j, all tiles for
-// i < j, each pair in bands of 8 row blocks (rows fastest in a band).
+// Tile lists of the slice products, in one of two forms.
+//  * Grouped (k = floor((2^24 - 1) / (31^2 r)) >= 2): for each order o the
+//    products (i, o - i) are packed into symmetric groups of at most
+//    min(k, kMaxGroupSeg) segments -- the diagonal (o/2, o/2) as one segment,
+//    each cross pair as two -- and every group covers the upper triangle: tiles
+//    (g * TP + I, J), J >= I.
+//  * Per pair (k = 1, r > 8729): the diagonal pairs cover the upper triangle
+//    and the cross pairs every tile, in stacked coordinates (i * TP + I,
+//    j * TP + J).
+// Either way the entries are ordered by o, so the products with o < s are the
+// first slice_tile_count[s] entries; rows are walked in bands of 8 row blocks.
 int ensure_slice_tiles(sos_plan_s* p) {
     std::lock_guard<std::mutex> lock(p->mu);
     if (p->dev.slice_tiles2) return SOS_OK;
     const int TP = (int)ceil_div(p->N, 256), band = 8;
+    const int64_t kexact = (((int64_t)1 << 24) - 1) / (31 * 31 * p->r);
+    const bool grouped = kexact >= 2;
+    const int kseg = (int)std::min<int64_t>(kexact, kMaxGroupSeg);
     std::vector<int2> t;
+    std::vector<SliceGroup> groups;
     int count[kMaxSlices + 1] = {0};
     int u = 0;
+    auto upper = [&](int xoff, int yoff) {
+        for (int i0 = 0; i0 < TP; i0 += band) {
+            const int i1 = std::min(TP, i0 + band);
+            for (int J = i0; J < TP; ++J)
+                for (int I = i0; I < i1; ++I)
+                    if (J >= I) t.push_back(make_int2(xoff + I, yoff + J));
+        }
+    };
     for (int o = 0; o < kMaxSlices; ++o) {
-        for (int i = 0; 2 * i <= o; ++i) {
-            const int j = o - i;
-            p->dev.slice_pair_offset[u++] = (int)t.size();
-            for (int i0 = 0; i0 < TP; i0 += band) {
-                const int i1 = std::min(TP, i0 + band);
-                for (int J = (i == j ? i0 : 0); J < TP; ++J)
-                    for (int I = i0; I < i1; ++I)
-                        if (i != j || J >= I) t.push_back(make_int2(i * TP + I, j * TP + J));
+        if (grouped) {
+            SliceGroup g{};
+            g.order = o;
+            auto flush = [&]() {
+                if (g.nseg == 0) return;
+                upper((int)groups.size() * TP, 0);
+                groups.push_back(g);
+                g = SliceGroup{};
+                g.order = o;
+            };
+            for (int i = o / 2; i >= 0; --i) {            // the diagonal first, when o is even
+                const int j = o - i;
+                const int need = i == j ? 1 : 2;
+                if (g.nseg + need > kseg) flush();
+                g.sa[g.nseg] = i;
+                g.sb[g.nseg] = j;
+                ++g.nseg;
+                if (i != j) {
+                    g.sa[g.nseg] = j;
+                    g.sb[g.nseg] = i;
+                    ++g.nseg;
+                }
+            }
+            flush();
+        } else {
+            for (int i = 0; 2 * i <= o; ++i) {
+                const int j = o - i;
+                p->dev.slice_pair_offset[u++] = (int)t.size();
+                for (int i0 = 0; i0 < TP; i0 += band) {
+                    const int i1 = std::min(TP, i0 + band);
+                    for (int J = (i == j ? i0 : 0); J < TP; ++J)
+                        for (int I = i0; I < i1; ++I)
+                            if (i != j || J >= I) t.push_back(make_int2(i * TP + I, j * TP + J));
+                }
             }
         }
         count[o + 1] = (int)t.size();
@@ -134,13 +180,20 @@ int ensure_slice_tiles(sos_plan_s* p) {
     p->dev.slice_pair_offset[u] = (int)t.size();
     p->dev.slice_pairs = u;
     int2* d = nullptr;
+    SliceGroup* dg = nullptr;
     cudaError_t e = cudaMalloc(&d, t.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMemcpy(d, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && grouped) e = cudaMalloc(&dg, groups.size() * sizeof(SliceGroup));
+    if (e == cudaSuccess && grouped)
+        e = cudaMemcpy(dg, groups.data(), groups.size() * sizeof(SliceGroup), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(d);
+        cudaFree(dg);
         return cuda_fail(e, "SOS_FP64_TC: tile list");
     }
     p->dev.slice_tiles2 = d;
+    p->dev.slice_groups = dg;
+    p->dev.slice_grouped = grouped;
     for (int s = 0; s <= kMaxSlices; ++s) p->dev.slice_tile_count[s] = count[s];
     return SOS_OK;
 }
@@ -181,6 +234,9 @@ int forward_tc64(sos_plan_s* p, const double* A, void* ws, double* c, int slices
                                                                reinterpret_cast<__nv_bfloat16*>(base + w.a16));
     }
     SOS_CUDA(cudaGetLastError());
+    if (p->dev.slice_grouped)
+        return launch_tc_slice_groups_pair(p, S, NP, p->dev.slice_tiles2, p->dev.slice_tile_count[slices],
+                                           p->dev.slice_groups, ex, c, status, st);
     // Every pair with i + j < slices.  Small plans run them all in one
     // persistent launch (a pair alone would leave most of its last wave of
     // CTA pairs idle); when one pair alone fills at least 8 waves, one launch

@@ -33,6 +33,7 @@ constexpr int STAGE_LD = 33;
 // All 32 index loads are issued before the first atomic, so they overlap.
 struct SegmentSumEpilogue {
     static constexpr const char* kName = "tc_forward";
+    static constexpr bool kSegmented = false;
     int N;
     const int32_t* idx;
     int64_t ld_idx;
@@ -75,6 +76,7 @@ __device__ __forceinline__ double pow2_int(int e) {
 // (i < j) cover every ordered (a, b) with weight 2, which also counts (j, i).
 struct SliceSumEpilogue {
     static constexpr const char* kName = "tc_slices";
+    static constexpr bool kSegmented = false;
     int N, NP;
     const int32_t* idx;
     int64_t ld_idx;
@@ -107,9 +109,63 @@ struct SliceSumEpilogue {
     }
 };
 
+// SOS_FP64_TC for plans with r 31^2 k < 2^24, k >= 2: a group sums k slice
+// products of one order o = i + j in a single accumulator (the sum of k exact
+// integers below 2^24 / k is still exact).  The tile's K runs over the group's
+// segments one after another -- segment s multiplies slice sa[s] (rows) with
+// slice sb[s] (columns), both from the stacked slices -- and every group is
+// symmetric: a diagonal product (i, i), or a cross product as the two segments
+// (i, j) and (j, i).  So each group needs only the upper triangle, with weights
+// 1 (a = b) and 2 (a < b), and one FP64 atomic per output element for all its
+// products.  Tiles are (g * TP + I, J), g the group.
+struct SliceGroupEpilogue {
+    static constexpr const char* kName = "tc_slices";
+    static constexpr bool kSegmented = true;
+    int N, NP, TP;
+    const int32_t* idx;
+    int64_t ld_idx;
+    double* c;
+    const int32_t* ex;
+    const SliceGroup* groups;
+
+    __device__ __forceinline__ int segments(int2 tile) const { return groups[tile.x / TP].nseg; }
+    // first stacked row of the pair tile in the segment's A and B operands
+    __device__ __forceinline__ int seg_arow(int2 tile, int seg) const {
+        const int g = tile.x / TP;
+        return groups[g].sa[seg] * NP + (tile.x - g * TP) * 256;
+    }
+    __device__ __forceinline__ int seg_brow(int2 tile, int seg) const {
+        return groups[tile.x / TP].sb[seg] * NP + tile.y * 256;
+    }
+
+    __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
+        const int g = a0 / NP;
+        const int al = a0 - g * NP;
+        if (al >= N || b0 >= N || b0 + 31 < al) return;
+        const int b = b0 + lane;
+        if (b >= N) return;
+        const int eb = ex[b] - 5 * (groups[g].order + 2);
+        const int32_t* col = idx + (int64_t)al * ld_idx + b;
+        int32_t gi[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int a = al + i;
+            gi[i] = (a < N && a <= b) ? __ldg(col + (int64_t)i * ld_idx) : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (gi[i] >= 0) {
+                const double v = (double)stage[i * STAGE_LD + lane] * pow2_int(ex[al + i] + eb);
+                atomicAdd(c + gi[i], al + i != b ? 2.0 * v : v);
+            }
+        }
+    }
+};
+
 // Adjoint / diagnostic GEMM: out[row][col] = scale * acc.
 struct StoreEpilogue {
     static constexpr const char* kName = "tc_adjoint";
+    static constexpr bool kSegmented = false;
     int rows, cols;
     int64_t ld;
     float scale;
@@ -137,6 +193,7 @@ struct DiagEpilogue : StoreEpilogue {
 // is still being read as an operand by other tiles).
 struct UpdateEpilogue {
     static constexpr const char* kName = "tc_adjoint_update";
+    static constexpr bool kSegmented = false;
     int rows, cols, optimizer;
     float lr, b1, b2, eps, c1, c2;
     float* A;

@@ -71,8 +71,13 @@ def problem(n, two_d, r, seed=0, sigma=0.3, spread=True):
     return o, A, p
 
 
+# r decides the form of the slice products: k = floor((2^24 - 1) / (31^2 r)) products
+# share an accumulator (k >= 2: grouped, upper triangle), or each pair alone (k = 1)
 @pytest.mark.parametrize("n,two_d,r", [(3, 4, 10), (4, 6, 35), (6, 8, 210), (5, 6, 300), (9, 6, 700),
-                                       (2, 10, 21)])
+                                       (2, 10, 21),
+                                       (7, 8, 5000),     # k = 3: a cross pair and the diagonal together
+                                       (2, 4, 6000),     # k = 2: one cross pair per group
+                                       (7, 8, 9000)])    # k = 1: one pair per product, cross pairs on all tiles
 def test_fp64_tc_forward_matches_oracle(n, two_d, r):
     o, A, _ = problem(n, two_d, r)
     pl = Plan(n, two_d, r)
