@@ -329,14 +329,15 @@ typedef struct {
  * BF16 (tc_fp64 = 1). */
 int sos_solve_opts_default(sos_solve_opts* opts);
 
-/* Minimises 1/2 ||c(A) - p||^2 from the start point A by the precision
- * ladder: BF16 steps until the relative residual falls below switch_rel (or
- * stalls), FP32 steps until they stall, FP64 steps on an FP64 copy of the
- * best FP32 point, then the FP64 certificate of the best checked point
- * (Sec. 3: success is the minimum error over the iterations).  The Adam
- * state carries over between stages.  A: dev N x r double, start point in,
- * best point out; p64: dev M double.  Allocates and frees its own buffers
- * and synchronises `stream`. */
+/* Minimises 1/2 ||c(A) - p||^2 from the start point A by a precision ladder:
+ * BF16 steps until the relative residual falls below switch_rel (or stalls),
+ * then SOS_FP64_TC steps on an FP64 copy of the best BF16 point (tc_fp64 = 1)
+ * -- or FP32 steps until they stall and FP64 steps on an FP64 copy of the
+ * best FP32 point (tc_fp64 = 0) -- then the FP64 certificate of the best
+ * checked point (Sec. 3: success is the minimum error over the iterations).
+ * The Adam state carries over between stages.  A: dev N x r double, start
+ * point in, best point out; p64: dev M double.  Allocates and frees its own
+ * buffers and synchronises `stream`. */
 int sos_solve(sos_plan_t plan, const double* p64, double* A, const sos_solve_opts* opts,
               sos_result* out, void* stream);
 
