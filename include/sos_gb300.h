@@ -294,7 +294,7 @@ typedef struct {
     double beta1, beta2, eps;
     int64_t max_steps;        /* step budget of the BF16 + FP32 stages */
     int64_t check_every;      /* evaluate the loss every K steps */
-    double switch_rel;        /* BF16 -> FP32 when ||c-p||/||p|| < switch_rel ... */
+    double switch_rel;        /* BF16 -> the next stage when ||c-p||/||p|| < switch_rel ... */
     int64_t stall_checks;     /* ... or after this many checks without a 1% gain;
                                  FP32 -> FP64 after as many */
     int64_t fp64_steps;       /* step budget of the FP64 stage (0: none) */
