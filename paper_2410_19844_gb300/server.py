@@ -86,7 +86,10 @@ class Policy:
     lr64: float = 1e-2
     cert_tol: float = 1e-8
     switch_rel: float = 1e-7         # FP32 -> FP64 at once below this
-    promote_rel: float = 1e-3        # ... or, when FP32 stalls, only below this
+    promote_rel: float = 1e-5        # ... or, when FP32 stalls, only below this: FP32 resolves
+                                     # residuals far above its ~1e-7 floor, so a stall above
+                                     # 1e-5 (after the step-size cuts) is the optimiser's, and
+                                     # FP64 steps would not reach the certificate either
     stall_checks: int = 3            # checks without a 1% gain
     decay: float = 0.1               # on a stall above target, scale the step size by this ...
     max_decays: int = 2              # ... at most this many times per stage before deciding
