@@ -360,6 +360,15 @@ typedef struct sos_group_s* sos_group_t;
  * step; the gradient it gives is accurate to FP32 relative to its own size. */
 #define SOS_GROUP_FP32_ADJOINT 1
 
+/* SOS_GROUP_FAST_FP64 (FP64 groups only) keeps FP64 arithmetic off the slow
+ * FP64 pipe where it is not needed.  The forward accumulates in double-float
+ * arithmetic on the FP32 pipes: products and sums are carried as two FP32
+ * words, with error-free products and two-sums, about 2^-46 relative to the
+ * sum of |products|.  The optimiser's update arithmetic runs in FP32, only when
+ * the adjoint does too (with SOS_GROUP_FP32_ADJOINT), and is subtracted from
+ * the FP64 iterate.  The residual, the loss and so the verdict stay FP64. */
+#define SOS_GROUP_FAST_FP64 2
+
 int sos_group_create(int prec, int capacity, int optimizer, double beta1, double beta2,
                      double eps, int flags, sos_group_t* out);
 int sos_group_destroy(sos_group_t group);

@@ -286,6 +286,7 @@ def sos_solve(plan, p64, A, opts: sos_solve_opts, stream) -> sos_result:
 
 
 SOS_GROUP_FP32_ADJOINT = 1
+SOS_GROUP_FAST_FP64 = 2
 
 
 def sos_group_create(prec, capacity, optimizer, beta1=0.9, beta2=0.999, eps=1e-8, flags=0) -> int:

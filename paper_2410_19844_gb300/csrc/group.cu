@@ -22,6 +22,8 @@
 #include <map>
 #include <vector>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace sos {
@@ -112,6 +114,89 @@ group_forward(const int* __restrict__ counts, const Item* __restrict__ items, co
     }
 }
 
+// FP64 groups with SOS_GROUP_FAST_FP64: the same forward in double-float
+// arithmetic on the FP32 pipes (the FP64 pipe is slow on this GPU).  Each entry
+// x of A is split into hi = float(x) and lo = float(x - hi) (48 of its 53
+// bits).  A product a b is hi_a hi_b, taken exactly as p + e with
+// e = fma(hi_a, hi_b, -p), plus the cross terms hi_a lo_b + lo_a hi_b; the sum
+// runs as a pair (s, t): s by a two-sum of s and p, whose rounding error goes
+// into t with e and the cross terms.  G = s + t in double is accurate to about
+// 2^-46 of the sum of |products|.  The explicit _rn intrinsics keep the compiler
+// from fusing the error-free steps into other multiply-adds.
+__global__ void __launch_bounds__(kT)
+group_forward_df(const int* __restrict__ counts, const Item* __restrict__ items,
+                 const Inst<double>* __restrict__ insts, const long long* __restrict__ step) {
+    __shared__ float Ah[16][65], Al[16][65], Bh[16][65], Bl[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int n_items = counts[0];
+    const long long now = *step;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const Item it = items[w];
+        const Inst<double>& in = insts[it.inst];
+        const int N = in.N, r = in.r;
+        const double* A = ((now - in.join) & 1) ? in.A1 : in.A0;
+        const int row0 = it.i * 64, col0 = it.j * 64;
+        float sh[4][4], sl[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.0f;
+        for (int k0 = 0; k0 < r; k0 += 16) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int e = tid + l * kT, rr = e >> 4, kk = e & 15;
+                const int gk = k0 + kk, ga = row0 + rr, gb = col0 + rr;
+                const double xa = (ga < N && gk < r) ? A[(int64_t)ga * r + gk] : 0.0;
+                const double xb = (gb < N && gk < r) ? A[(int64_t)gb * r + gk] : 0.0;
+                const float ha = __double2float_rn(xa), hb = __double2float_rn(xb);
+                Ah[kk][rr] = ha;
+                Al[kk][rr] = __double2float_rn(xa - (double)ha);
+                Bh[kk][rr] = hb;
+                Bl[kk][rr] = __double2float_rn(xb - (double)hb);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < 16; ++kk) {
+                float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ah[i] = Ah[kk][ty + 16 * i];
+                    al[i] = Al[kk][ty + 16 * i];
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    bh[j] = Bh[kk][tx + 16 * j];
+                    bl[j] = Bl[kk][tx + 16 * j];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float p = __fmul_rn(ah[i], bh[j]);
+                        const float e = __fmaf_rn(ah[i], bh[j], -p);
+                        const float q = __fmaf_rn(ah[i], bl[j], __fmaf_rn(al[i], bh[j], e));
+                        const float t = __fadd_rn(sh[i][j], p);
+                        const float z = __fsub_rn(t, sh[i][j]);
+                        const float err = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));
+                        sh[i][j] = t;
+                        sl[i][j] = __fadd_rn(sl[i][j], __fadd_rn(err, q));
+                    }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int a = row0 + ty + 16 * i;
+            if (a >= N) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int b = col0 + tx + 16 * j;
+                if (b < N) in.G[(int64_t)a * N + b] = (double)sh[i][j] + (double)sl[i][j];
+            }
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kT)
 group_residual(const int* __restrict__ counts, const Item* __restrict__ items, int cap,
@@ -165,7 +250,7 @@ group_residual(const int* __restrict__ counts, const Item* __restrict__ items, i
 // Tc is the type of the contraction (T, or float for an FP64 group that
 // takes its gradient from the FP64 residual in FP32 arithmetic); the update
 // and the iterate stay in T.
-template <typename T, typename Tc>
+template <typename T, typename Tc, typename U = T>
 __global__ void __launch_bounds__(kT)
 group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, int cap,
               const Inst<T>* __restrict__ insts, const long long* __restrict__ step, int optimizer, double b1,
@@ -218,9 +303,11 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
             }
             __syncthreads();
         }
+        // the update's arithmetic runs in U (T, or float for SOS_GROUP_FAST_FP64);
+        // the iterate and the moments are stored in T
         const double t = (double)(taken + in.t0 + 1);
-        const T c1 = (T)(1.0 - pow(b1, t)), c2 = (T)(1.0 - pow(b2, t));
-        const T lr = (T)in.lr, B1 = (T)b1, B2 = (T)b2, EPS = (T)eps, one = T(1);
+        const U c1 = (U)(1.0 - pow(b1, t)), c2 = (U)(1.0 - pow(b2, t));
+        const U lr = (U)in.lr, B1 = (U)b1, B2 = (U)b2, EPS = (U)eps, one = U(1);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int a = row0 + ty + 16 * i;
@@ -230,18 +317,18 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
                 const int k = col0 + tx + 16 * j;
                 if (k >= r) continue;
                 const int64_t e = (int64_t)a * r + k;
-                const T g = T(2) * (T)acc[i][j];
-                T x = A[e];
+                const U g = U(2) * (U)acc[i][j];
+                U step_;
                 if (optimizer == SOS_GD) {
-                    x -= lr * g;
+                    step_ = lr * g;
                 } else {
-                    const T mi = B1 * in.m[e] + (one - B1) * g;
-                    const T vi = B2 * in.v[e] + (one - B2) * g * g;
-                    in.m[e] = mi;
-                    in.v[e] = vi;
-                    x -= lr * (mi / c1) / (sqrt(vi / c2) + EPS);
+                    const U mi = B1 * (U)in.m[e] + (one - B1) * g;
+                    const U vi = B2 * (U)in.v[e] + (one - B2) * g * g;
+                    in.m[e] = (T)mi;
+                    in.v[e] = (T)vi;
+                    step_ = lr * (mi / c1) / (sqrt(vi / c2) + EPS);
                 }
-                A_next[e] = x;
+                A_next[e] = A[e] - (T)step_;
             }
         }
     }
@@ -293,6 +380,7 @@ using namespace sos::grp;
 struct sos_group_s {
     int prec = SOS_FP32;
     bool fp32_adjoint = false;    // FP64 group: contraction of the adjoint in FP32
+    bool fast_fp64 = false;       // FP64 group: double-float forward, FP32 update arithmetic
     int capacity = 0;
     int optimizer = SOS_ADAM;
     double b1 = 0.9, b2 = 0.999, eps = 1e-8;
@@ -391,7 +479,14 @@ int launch_step(sos_group_s* g, cudaStream_t st) {
     const Inst<T>* insts = static_cast<const Inst<T>*>(g->d_insts);
     {
         KernelScope ks_("group_forward", st);
-        group_forward<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
+        if constexpr (std::is_same<T, double>::value) {
+            if (g->fast_fp64)
+                group_forward_df<<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
+            else
+                group_forward<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
+        } else {
+            group_forward<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
+        }
     }
     {
         KernelScope ks_("group_residual", st);
@@ -399,7 +494,10 @@ int launch_step(sos_group_s* g, cudaStream_t st) {
     }
     {
         KernelScope ks_("group_adjoint", st);
-        if (g->fp32_adjoint)
+        if (g->fp32_adjoint && g->fast_fp64)
+            group_adjoint<T, float, float><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts,
+                                                                   g->d_step, g->optimizer, g->b1, g->b2, g->eps);
+        else if (g->fp32_adjoint)
             group_adjoint<T, float><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
                                                             g->optimizer, g->b1, g->b2, g->eps);
         else
@@ -429,12 +527,13 @@ int sos_group_scratch_size(sos_plan_t p, int prec, size_t* bytes) {
 int sos_group_create(int prec, int capacity, int optimizer, double beta1, double beta2, double eps, int flags,
                      sos_group_t* out) {
     if (!out || (prec != SOS_FP32 && prec != SOS_FP64) || capacity < 1 || capacity > (1 << 20) ||
-        (optimizer != SOS_ADAM && optimizer != SOS_GD) || (flags & ~SOS_GROUP_FP32_ADJOINT))
+        (optimizer != SOS_ADAM && optimizer != SOS_GD) || (flags & ~(SOS_GROUP_FP32_ADJOINT | SOS_GROUP_FAST_FP64)))
         return fail(SOS_E_INVALID, "sos_group_create: bad argument");
     *out = nullptr;
     sos_group_s* g = new sos_group_s();
     g->prec = prec;
     g->fp32_adjoint = prec == SOS_FP64 && (flags & SOS_GROUP_FP32_ADJOINT);
+    g->fast_fp64 = prec == SOS_FP64 && (flags & SOS_GROUP_FAST_FP64);
     g->capacity = capacity;
     g->optimizer = optimizer;
     g->b1 = beta1;

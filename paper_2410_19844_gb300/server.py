@@ -105,7 +105,8 @@ def _footprint(plan: Plan, elt: int) -> int:
 
 class Server:
     def __init__(self, capacity: int = 256, hbm_budget: int = 16 << 30, steps_per_tick: int = 32,
-                 policy: Optional[Policy] = None, optimizer: str = "adam", fp32_adjoint: bool = True):
+                 policy: Optional[Policy] = None, optimizer: str = "adam", fp32_adjoint: bool = True,
+                 fast_fp64: bool = True):
         self.capacity = capacity
         self.budget = hbm_budget
         self.K = steps_per_tick
@@ -113,7 +114,8 @@ class Server:
         opt = L.SOS_ADAM if optimizer == "adam" else L.SOS_GD
         self.g32 = L.sos_group_create(L.SOS_FP32, capacity, opt)
         self.g64 = L.sos_group_create(L.SOS_FP64, capacity, opt,
-                                      flags=L.SOS_GROUP_FP32_ADJOINT if fp32_adjoint else 0)
+                                      flags=(L.SOS_GROUP_FP32_ADJOINT if fp32_adjoint else 0)
+                                      | (L.SOS_GROUP_FAST_FP64 if fast_fp64 else 0))
         self.plans: dict = {}
         self.free32 = list(range(capacity))[::-1]
         self.free64 = list(range(capacity))[::-1]

@@ -45,10 +45,10 @@ def make_request(rid, n, two_d, sos, arrival=0.0):
     return Job(rid, arrival, n, two_d, make)
 
 
-def _group_run(prec, jobs, steps):
+def _group_run(prec, jobs, steps, flags=0):
     """Runs `jobs` together in one group; returns each one's current A."""
     dt = torch.float64 if prec == L.SOS_FP64 else torch.float32
-    g = L.sos_group_create(prec, len(jobs), L.SOS_ADAM)
+    g = L.sos_group_create(prec, len(jobs), L.SOS_ADAM, flags=flags)
     keep, plans = [], {}
     st = _stream_handle()
     for s, job in enumerate(jobs):
@@ -87,6 +87,30 @@ def test_iterates_identical_alone_and_mixed(prec):
     alone, _ = _group_run(prec, [target], 40)
     mixed, _ = _group_run(prec, others[:2] + [target] + others[2:], 40)
     assert np.array_equal(alone[0], mixed[2])
+
+
+FAST = L.SOS_GROUP_FP32_ADJOINT | L.SOS_GROUP_FAST_FP64
+
+
+def test_fast_fp64_iterates_identical_alone_and_mixed():
+    target = make_request(7, 5, 6, True)
+    others = [make_request(10 + i, n, d, i % 2 == 0) for i, (n, d) in
+              enumerate([(3, 4), (8, 8), (6, 8), (4, 6), (7, 4)])]
+    alone, _ = _group_run(L.SOS_FP64, [target], 40, FAST)
+    mixed, _ = _group_run(L.SOS_FP64, others[:2] + [target] + others[2:], 40, FAST)
+    assert np.array_equal(alone[0], mixed[2])
+
+
+@pytest.mark.parametrize("n,two_d", [(4, 6), (8, 8)])
+def test_fast_fp64_loss_matches_oracle(n, two_d):
+    """The double-float forward: the loss of the start point within 1e-11 of the
+    oracle's FP64 loss (about 2^-46 per coefficient, relative to its |products|)."""
+    job = make_request(21, n, two_d, True)
+    o = _oracle(n, two_d)
+    p64, A0 = job.make()
+    _, losses = _group_run(L.SOS_FP64, [job], 1, FAST)
+    loss_ref = o.loss(A0.cpu().numpy(), p64.cpu().numpy())
+    assert abs(losses[0] - loss_ref) <= 1e-11 * loss_ref
 
 
 def test_group_fp64_step_matches_oracle():
