@@ -15,14 +15,21 @@
 //     dL/dP_k[i][j] = dL/dA_hat[(min, max)(i, j)][k]      (the symmetric S_k)
 //     dL/dB (as the stack of M_k) = S A1^T,   dL/dA1 = sum_k M_k^T S_k,
 // three plain GEMMs with B viewed as a (k nf) x m matrix.  They are small next
-// to the core pass (k nf^2 m against k N^2 multiply-adds) and run on CUDA cores
-// in the step's precision (float for BF16 and FP32, double for FP64).
+// to the core pass (k nf^2 m against k N^2 multiply-adds).  In FP32 and FP64
+// they run on CUDA cores.  In BF16 steps with nf and m of 64 or more, the two
+// with k nf output rows -- P = B A1 and dL/dB = S A1^T -- run on the tensor
+// cores from bf16 copies of B, A1 and S (CTA pairs, FP32 accumulation), like
+// the core contractions; the long reduction dL/dA1 stays on CUDA cores (split
+// over K).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
+#include "tc_epilogues.cuh"
 
 namespace sos {
 namespace {
@@ -167,6 +174,35 @@ __global__ void form_scatter_kernel(const T* __restrict__ G, const int32_t* __re
     }
 }
 
+// bf16 copy of a rows x cols float matrix into rows of ld (ld >= cols).
+__global__ void cast_rows_bf16_kernel(const float* __restrict__ x, int64_t rows, int64_t cols,
+                                      __nv_bfloat16* __restrict__ y, int64_t ld) {
+    const int64_t count = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols, j = e - i * cols;
+        y[i * ld + j] = __float2bfloat16_rn(x[e]);
+    }
+}
+
+// S_kk[i][j] = G[rows[i][j]][kk] as bf16 into rows of ld (the tensor-core operand).
+__global__ void form_scatter_bf16_kernel(const float* __restrict__ G, const int32_t* __restrict__ rows, int64_t k,
+                                         int nf, __nv_bfloat16* __restrict__ S, int64_t ld) {
+    const int64_t count = k * nf * nf;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / nf;            // row kk * nf + i
+        const int j = (int)(e - r * nf), i = (int)(r % nf);
+        const int64_t kk = r / nf;
+        S[r * ld + j] = __float2bfloat16_rn(G[(int64_t)rows[i * nf + j] * k + kk]);
+    }
+}
+
+// The 256 x 256 output tiles (i, j) of a TI x TJ grid, row by row.
+__global__ void tile_grid_kernel(int TI, int TJ, int2* __restrict__ tiles) {
+    const int count = TI * TJ;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+        tiles[e] = make_int2(e / TJ, e % TJ);
+}
+
 int grid_for(int64_t count) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 16));
 }
@@ -187,6 +223,11 @@ struct LayerLayout {
     size_t gB = 0;      // k x nf*m
     size_t gA1 = 0;     // m x nf
     size_t part = 0;    // split partial sums of dL/dA1
+    // BF16 steps on CTA pairs: bf16 operands of the two tensor-core GEMMs and their tile lists
+    size_t B16 = 0, A116 = 0, S16 = 0, tilesP = 0, tilesG = 0;
+    int64_t ldm = 0, ldnf = 0;
+    int ntP = 0, ntG = 0;
+    bool tc = false;
     size_t total = 0;
     int splits = 1;
     int64_t kchunk = 0;
@@ -214,6 +255,22 @@ LayerLayout layer_layout(const sos_plan_s* p, int prec, int m) {
     w.kchunk = ((K + w.splits - 1) / w.splits + kBK - 1) / kBK * kBK;
     w.splits = (int)((K + w.kchunk - 1) / w.kchunk);
     w.part = take((size_t)w.splits * m * nf * elt);
+    // below 64 form variables or first-layer outputs the 256 x 256 tensor-core
+    // tiles are mostly padding and the extra casts cost more than they save
+    // (measured: nf = 31 slower by 13%, nf = 101 faster by 8%)
+    w.tc = prec == SOS_BF16 && use_cta_pairs() && nf >= 64 && m >= 64;
+    if (w.tc) {
+        w.ldm = round_up(m, 64);
+        w.ldnf = round_up(nf, 64);
+        w.B16 = take((size_t)K * w.ldm * 2);
+        w.A116 = take((size_t)m * w.ldnf * 2);
+        w.S16 = take((size_t)K * w.ldnf * 2);
+        const int64_t TI = ceil_div(K, 256);
+        w.ntP = (int)(TI * ceil_div(nf, 256));
+        w.ntG = (int)(TI * ceil_div(m, 256));
+        w.tilesP = take((size_t)w.ntP * sizeof(int2));
+        w.tilesG = take((size_t)w.ntG * sizeof(int2));
+    }
     w.total = off;
     return w;
 }
@@ -286,8 +343,27 @@ template <typename T>
 int expand(sos_plan_s* p, int m, const T* B, const T* A1, T* Ahat, const LayerLayout& w, void* ws, cudaStream_t st) {
     const int64_t nf = p->n + 1, k = p->r;
     T* P = at<T>(ws, w.P);
-    // (k nf) x m times m x nf
-    SOS_CHECK(launch_gemm<T>(k * nf, nf, m, m, 1, B, m, 1, A1, nf, 1, P, nf, 0, st));
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (w.tc) {   // BF16 step: bf16 copies of B and A1, then (k nf) x m times m x nf on tensor cores
+            auto* B16 = at<__nv_bfloat16>(ws, w.B16);
+            auto* A116 = at<__nv_bfloat16>(ws, w.A116);
+            int2* tiles = at<int2>(ws, w.tilesP);
+            {
+                KernelScope ks_("layer_cast", st);
+                cast_rows_bf16_kernel<<<grid_for(k * nf * m), 256, 0, st>>>(B, k * nf, m, B16, w.ldm);
+                cast_rows_bf16_kernel<<<grid_for((int64_t)m * nf), 256, 0, st>>>(A1, m, nf, A116, w.ldnf);
+                tile_grid_kernel<<<grid_for(w.ntP), 256, 0, st>>>((int)ceil_div(k * nf, 256), (int)ceil_div(nf, 256),
+                                                                 tiles);
+            }
+            SOS_CUDA(cudaGetLastError());
+            int32_t* status = at<int32_t>(ws, w.core + workspace_layout(p, SOS_BF16).status);
+            SOS_CHECK(diag_gemm_pair(1, B16, A116, P, k * nf, nf, m, w.ldm, w.ldnf, tiles, w.ntP, status, st));
+            done = true;
+        }
+    }
+    if (!done)   // (k nf) x m times m x nf
+        SOS_CHECK(launch_gemm<T>(k * nf, nf, m, m, 1, B, m, 1, A1, nf, 1, P, nf, 0, st));
     {
         KernelScope ks_("layer_expand", st);
         form_expand_kernel<T><<<grid_for(p->N * k), 256, 0, st>>>(P, p->dev.form_pairs, p->N, k, (int)nf, Ahat);
@@ -307,7 +383,26 @@ int pull_back(sos_plan_s* p, int m, const T* B, const T* A1, const T* gAhat, T* 
         form_scatter_kernel<T><<<grid_for(k * nf * nf), 256, 0, st>>>(gAhat, p->dev.form_rows, k, (int)nf, S);
     }
     SOS_CUDA(cudaGetLastError());
-    if (gB)   // S (k nf x nf) times A1^T (nf x m)
+    bool gb_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (w.tc && gB) {   // BF16 step: S in bf16, then (k nf) x nf times (m x nf)^T on tensor cores
+            auto* S16 = at<__nv_bfloat16>(ws, w.S16);
+            auto* A116 = at<__nv_bfloat16>(ws, w.A116);   // cast by expand() in this pass
+            int2* tiles = at<int2>(ws, w.tilesG);
+            {
+                KernelScope ks_("layer_scatter", st);
+                form_scatter_bf16_kernel<<<grid_for(k * nf * nf), 256, 0, st>>>(gAhat, p->dev.form_rows, k, (int)nf,
+                                                                               S16, w.ldnf);
+                tile_grid_kernel<<<grid_for(w.ntG), 256, 0, st>>>((int)ceil_div(k * nf, 256), (int)ceil_div(m, 256),
+                                                                 tiles);
+            }
+            SOS_CUDA(cudaGetLastError());
+            int32_t* status = at<int32_t>(ws, w.core + workspace_layout(p, SOS_BF16).status);
+            SOS_CHECK(diag_gemm_pair(0, S16, A116, gB, k * nf, m, nf, w.ldnf, w.ldnf, tiles, w.ntG, status, st));
+            gb_done = true;
+        }
+    }
+    if (gB && !gb_done)   // S (k nf x nf) times A1^T (nf x m)
         SOS_CHECK(launch_gemm<T>(k * nf, m, nf, nf, 1, S, nf, 1, A1, 1, nf, gB, m, 0, st));
     if (gA1) {  // B^T (m x k nf) times S (k nf x nf), split along k nf
         T* part = at<T>(ws, w.part);

@@ -5,10 +5,12 @@ first-layer width m = nf and 2 nf, FP32 and BF16 steps (Adam).
 
 Each configuration: 3 warm-up steps, then 10 timed steps with per-kernel CUDA
 events (sos_timing_*) and the whole-step time from events around the loop.
-The first layer's three GEMMs (kernel "layer_gemm") do 6 k nf^2 m flops per
-step on the CUDA cores; their rate is compared with the FP32 FMA peak of the
+The first layer's three GEMMs do 6 k nf^2 m flops per step: on the CUDA cores
+("layer_gemm"), and in BF16 steps with nf, m >= 64 two of them on the tensor
+cores ("tc_gemm_diag").  Their rate is compared with the FP32 FMA peak of the
 GPU, 152 SMs x 128 lanes x 2 flops x the SM clock (given on the command line,
-default 1.9 GHz).  The core pass does 3 N^2 k flops.
+default 1.9 GHz) -- for the mixed BF16 rows that ratio is only indicative.
+The core pass does 3 N^2 k flops.
 
     python tests/report_layer_timing.py [--clock-ghz 1.9] [--out FILE]
 """
@@ -63,8 +65,11 @@ def main():
                 L.sos_timing_enable(False)
                 rep = L.sos_timing_report()
                 step_ms = e0.elapsed_time(e1) / steps
-                gemm_ms = rep.get("layer_gemm", (0, 0.0))[1] / steps
-                core_names = [k for k in rep if not k.startswith("layer_") and k != "update"]
+                # the layer's GEMMs: CUDA-core "layer_gemm", and in BF16 steps with nf, m >= 64 the
+                # tensor-core products "tc_gemm_diag"
+                gemm_ms = (rep.get("layer_gemm", (0, 0.0))[1] + rep.get("tc_gemm_diag", (0, 0.0))[1]) / steps
+                core_names = [k for k in rep
+                              if not k.startswith("layer_") and k not in ("update", "tc_gemm_diag")]
                 core_ms = sum(rep[k][1] for k in core_names) / steps
                 layer_flops = 6.0 * N * nf * nf * m
                 core_flops = 3.0 * N * N * N

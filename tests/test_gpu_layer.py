@@ -7,8 +7,9 @@ Tolerances (from the arithmetic):
   * FP32: A_hat within 1e-6 relative, loss and gradients within 1e-5
     (normwise), the core path's FP32 tolerance;
   * BF16: the core contractions see A_hat rounded to bf16 and the residual
-    rounded to bf16 (2^-8 each), so loss and gradients are compared normwise at
-    2e-2 -- the core BF16 path itself is checked elementwise elsewhere.
+    rounded to bf16 (2^-8 each), and with nf, m >= 64 the layer's GEMMs read
+    bf16 B, A1 and S too, so loss and gradients are compared normwise at 2e-2
+    -- the core BF16 path itself is checked elementwise elsewhere.
 Shapes cover m < nf, m = nf, m = 2 nf, k not a multiple of 64, and a
 (k nf)-deep reduction that is split over many blocks.
 """
@@ -76,7 +77,8 @@ def test_layer_loss_grad_fp32(nf, m, k):
     assert rel(gA1.cpu().numpy(), gA1_ref) < 1e-5
 
 
-@pytest.mark.parametrize("nf,m,k", [(6, 12, 21), (11, 22, 200)])
+@pytest.mark.parametrize("nf,m,k", [(6, 12, 21), (11, 22, 200),
+                                    (64, 70, 20)])     # nf, m >= 64: P and dL/dB on the tensor cores
 def test_layer_loss_grad_bf16(nf, m, k):
     o, B, A1, p = case(nf, m, k)
     B32, A132, p32 = B.astype(np.float32), A1.astype(np.float32), p.astype(np.float32)
