@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--lr", type=float, default=1e-7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of the end-to-end timing (default: --steps, so both run as long)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=4096)
     ap.add_argument("--latency-requests", type=int, default=512)
@@ -453,7 +454,7 @@ def run_ours(args):
         A_host = A0.clone().pin_memory()
         p_host = p.cpu().pin_memory()
         loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
-        k2 = max(1, min(args.e2e_steps, args.steps))
+        k2 = max(1, args.e2e_steps if args.e2e_steps > 0 else args.steps)
 
         def timed(step_fn):
             for _ in range(2):
