@@ -101,7 +101,7 @@ struct DeviceTables {
     int num_fwd_tiles = 0;
     int num_adj_tiles = 0;
     int2* fwd_tiles2 = nullptr;  // the same in 256 x 256 tiles, for CTA pairs
-    int2* adj_tiles2 = nullptr;
+    int2* adj_tiles2 = nullptr;  // entries with y < 0: narrow tiles, 128 columns from 128 (-y - 1)
     int num_fwd_tiles2 = 0;
     int num_adj_tiles2 = 0;
     // pair lists of the Gram identity, grouped by coefficient (built on demand):
@@ -191,6 +191,9 @@ int launch_tc_adjoint_pair(const sos_plan_s* plan, const void* h16, const void* 
 int launch_tc_adjoint_update_pair(const sos_plan_s* plan, const void* h16, const void* a16_cur, void* a16_next,
                                   float* A, float* m, float* v, int optimizer, int64_t t, double lr, double b1,
                                   double b2, double eps, int32_t* status, cudaStream_t st);
+// How many CTA pairs of the adjoint kernel are resident on the current GPU at
+// once (the persistent grid of its launches).
+int adjoint_pair_capacity(int* pairs);
 
 // ---- one pass of the objective (api.cu), shared with the first layer ----------
 

@@ -16,6 +16,13 @@
 // Every mbarrier wait is bounded by the global timer; a role that gives up sets
 // the status word and unwinds, and both CTAs still meet at the final cluster
 // barrier before TMEM is released.
+//
+// A tile entry (x, y) is row block x of 256 and column block y of 256.  An
+// entry with y < 0 is a narrow tile: columns 128 (-y - 1) onwards, 128 wide,
+// computed with N = 128 MMAs (each CTA supplies 64 columns of B).  The tile
+// lists use narrow tiles to even out the last round of a persistent launch.
+// The producer still loads the full B boxes for a narrow tile (the MMAs read
+// only their first 64 columns or rows), so every stage expects the same bytes.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -111,8 +118,10 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
         bool ok = true;
         for (int t = pair; t < num_tiles && ok; t += num_pairs) {
             const int2 tile = tiles[t];
+            const bool narrow = tile.y < 0;
             const int arow = tile.x * PAIR_M + (int)rank * BM;
-            const int bcol = tile.y * BN + (int)rank * (BN / 2);
+            const int bcol = narrow ? (-tile.y - 1) * (BN / 2) + (int)rank * (BN / 4)
+                                    : tile.y * BN + (int)rank * (BN / 2);
             int nkbt = nkb;       // K blocks of this tile (all its segments)
             if constexpr (Epilogue::kSegmented) nkbt = epi.segments(tile) * nkb;
             for (int kb = 0; kb < nkbt; kb += KATOMS) {
@@ -162,12 +171,17 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 mbar_wait(&full[i % STAGES], (uint32_t)((i / STAGES) & 1), WAIT_LIMIT_NS);
     } else if (warp == 1 && lane == 0 && leader) {
         // ---------------- MMA issuer (leader) ----------------
-        constexpr uint32_t idesc = idesc_bf16_f32(PAIR_M, BN, 0, B_MN_MAJOR ? 1 : 0);
+        constexpr uint32_t idesc_full = idesc_bf16_f32(PAIR_M, BN, 0, B_MN_MAJOR ? 1 : 0);
+        constexpr uint32_t idesc_narrow = idesc_bf16_f32(PAIR_M, BN / 2, 0, B_MN_MAJOR ? 1 : 0);
         int s = 0;
         uint32_t ph = 0;
         int it = 0;
         bool ok = true;
+        // the next tile's entry is loaded one tile ahead, off the issue path
+        int2 next = pair < num_tiles ? tiles[pair] : make_int2(0, 0);
         for (int t = pair; t < num_tiles && ok; t += num_pairs, ++it) {
+            const int2 tile = next;
+            if (t + num_pairs < num_tiles) next = tiles[t + num_pairs];
             const int buf = it & 1;
             const uint32_t tph = (uint32_t)(it >> 1) & 1u;
             if (*err || !mbar_wait(&tempty[buf], tph ^ 1u, WAIT_LIMIT_NS)) {
@@ -176,8 +190,9 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             }
             tc_fence_after();
             const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
+            const uint32_t idesc = tile.y < 0 ? idesc_narrow : idesc_full;
             int nkbt = nkb;
-            if constexpr (Epilogue::kSegmented) nkbt = epi.segments(tiles[t]) * nkb;
+            if constexpr (Epilogue::kSegmented) nkbt = epi.segments(tile) * nkb;
             for (int kb = 0; kb < nkbt; kb += KATOMS) {
                 if (*err || !mbar_wait(&full[s], ph, WAIT_LIMIT_NS)) {
                     ok = false;
@@ -232,15 +247,17 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             const int2 tile = tiles[t];
             float* stage = epi_stage + (warp - 2) * 32 * STAGE_LD;
             const int row0 = tile.x * PAIR_M + (int)rank * BM + q * 32;
+            const int col0 = tile.y < 0 ? (-tile.y - 1) * (BN / 2) : tile.y * BN;
+            const int nch = tile.y < 0 ? BN / 64 : BN / 32;
 #pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ++ch) {
+            for (int ch = 0; ch < nch; ++ch) {
                 uint32_t v[32];
                 tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
                 tmem_ld_wait();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) stage[lane * STAGE_LD + j] = __uint_as_float(v[j]);
                 __syncwarp();
-                epi(row0, tile.y * BN + ch * 32, stage, lane);
+                epi(row0, col0 + ch * 32, stage, lane);
                 __syncwarp();
             }
             tc_fence_before();
@@ -268,14 +285,9 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
 
 namespace {
 
-template <bool B_MN, class Epi>
-int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
-                     const Epi& epi, int32_t* status, cudaStream_t st) {
+void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cudaStream_t st) {
     using namespace tc2;
-    static int max_pairs = -1;
-    auto kern = tc_gemm_pair_kernel<B_MN, Epi>;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cfg = {};
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
@@ -285,17 +297,37 @@ int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, cons
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (max_pairs < 0) {
-        SOS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        int dev = 0, sms = 0;
-        SOS_CUDA(cudaGetDevice(&dev));
-        SOS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        cfg.gridDim = dim3(sms);
-        int clusters = 0;
-        SOS_CUDA(cudaOccupancyMaxActiveClusters(&clusters, (void*)kern, &cfg));
-        if (clusters < 1) return fail(SOS_E_UNSUPPORTED, "CTA pairs: no cluster of two fits on this GPU");
-        max_pairs = clusters;     // every pair resident at once: the tile loop assumes it
-    }
+}
+
+// How many CTA pairs of `kern` fit on the current GPU at once.
+int resident_pairs(const void* kern, int* out) {
+    using namespace tc2;
+    SOS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    int dev = 0, sms = 0;
+    SOS_CUDA(cudaGetDevice(&dev));
+    SOS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    pair_launch_config(cfg, attr, 0);
+    cfg.gridDim = dim3(sms);
+    int clusters = 0;
+    SOS_CUDA(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
+    if (clusters < 1) return fail(SOS_E_UNSUPPORTED, "CTA pairs: no cluster of two fits on this GPU");
+    *out = clusters;
+    return SOS_OK;
+}
+
+template <bool B_MN, class Epi>
+int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
+                     const Epi& epi, int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    static int max_pairs = -1;
+    auto kern = tc_gemm_pair_kernel<B_MN, Epi>;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    pair_launch_config(cfg, attr, st);
+    // every pair resident at once: the tile loop assumes it
+    if (max_pairs < 0) SOS_CHECK(resident_pairs((const void*)kern, &max_pairs));
     if (num_tiles <= 0) return SOS_OK;
     const int pairs = num_tiles < max_pairs ? num_tiles : max_pairs;
     cfg.gridDim = dim3(2 * pairs);
@@ -307,6 +339,13 @@ int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, cons
 }
 
 }  // namespace
+
+int adjoint_pair_capacity(int* pairs) {
+    static int cached = -1;
+    if (cached < 0) SOS_CHECK(resident_pairs((const void*)tc2::tc_gemm_pair_kernel<true, tc::UpdateEpilogue>, &cached));
+    *pairs = cached;
+    return SOS_OK;
+}
 
 int launch_tc_forward_pair(const sos_plan_s* p, const void* a16, float* c, int32_t* status, cudaStream_t st) {
     using namespace tc2;

@@ -235,7 +235,7 @@ namespace sos {
 // i.e. J >= floor(I / 2).  The adjoint covers N x r in tiles of 128 x 256.
 // Both lists walk bands of row blocks so that the CTAs running at the same
 // time share operand panels in L2.
-static void make_tiles(const sos_plan_s* p, std::vector<int2>& fwd, std::vector<int2>& adj,
+static void make_tiles(const sos_plan_s* p, int pairs, std::vector<int2>& fwd, std::vector<int2>& adj,
                        std::vector<int2>& fwd2, std::vector<int2>& adj2) {
     const int TI = (int)ceil_div(p->N, 128), TJ = (int)ceil_div(p->N, 256);
     const int band = 16;
@@ -273,6 +273,23 @@ static void make_tiles(const sos_plan_s* p, std::vector<int2>& fwd, std::vector<
         for (int K = 0; K < TK; ++K)
             for (int I = i0; I < i1; ++I) adj2.push_back(make_int2(I, K));
     }
+    // The persistent adjoint gives tile t to pair t mod `pairs`, so a list of
+    // T tiles takes ceil(T / pairs) rounds, the last holding R = T mod pairs
+    // tiles.  When R <= pairs / 2, those R tiles become narrow 128-column
+    // halves (one half when the tile's valid width is at most 128); the last
+    // round then runs at most 2R half tiles on as many pairs and takes half
+    // as long.
+    const int T = (int)adj2.size();
+    const int R = pairs > 0 ? T % pairs : 0;
+    if (R > 0 && 2 * R <= pairs) {
+        std::vector<int2> tail(adj2.end() - R, adj2.end());
+        adj2.resize(T - R);
+        for (const int2& tl : tail) {
+            const int64_t w = std::min<int64_t>(256, p->r - (int64_t)tl.y * 256);
+            adj2.push_back(make_int2(tl.x, -(2 * tl.y + 1)));
+            if (w > 128) adj2.push_back(make_int2(tl.x, -(2 * tl.y + 2)));
+        }
+    }
 }
 
 bool use_cta_pairs() {
@@ -296,7 +313,9 @@ int ensure_device(sos_plan_s* p) {
     SOS_CUDA(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, cur));
     const size_t idx_bytes = (size_t)p->N * (size_t)p->ld_idx * sizeof(int32_t);
     std::vector<int2> fwd, adj, fwd2, adj2;
-    make_tiles(p, fwd, adj, fwd2, adj2);
+    int pairs = 0;
+    if (use_cta_pairs()) SOS_CHECK(adjoint_pair_capacity(&pairs));
+    make_tiles(p, pairs, fwd, adj, fwd2, adj2);
     uint8_t* d_S = nullptr;
     int32_t* d_phi = nullptr;
     cudaError_t e = cudaMalloc(&t.idx, idx_bytes);

@@ -287,6 +287,41 @@ def test_nonfinite_target_sets_status(prec):
 
 # -- the fused BF16 step (update inside the adjoint epilogue) --------------------------------
 
+@pytest.mark.parametrize("r", [4750, 4900])
+def test_bf16_adjoint_narrow_tail_tiles(r):
+    # N = 1001 (4 row blocks of 256) and r = 4750 or 4900 (19 or 20 column blocks):
+    # 76 or 80 adjoint tiles.  With 72 to 76 resident CTA pairs one of the two
+    # lists ends in a short last round, whose tiles run as 128-column halves;
+    # the last column block is 142 (two halves) or 36 (one half) wide.
+    # At this depth the forward's FP32 accumulation may truncate once per
+    # 16-deep MMA step, so the bounds are those of tests/test_gpu_fullsize.py:
+    # |dc| <= (r + N) u |c|(|A|) elementwise and (r / 16 + 64) u ||c(|A|)||
+    # normwise, u = 2^-23, carried through the BF16 residual into the gradient.
+    o, A, p = problem(10, 8, r)
+    A16 = bf16_round(A)
+    absA = np.abs(A16)
+    p32 = p.astype(np.float32).astype(np.float64)
+    pl = Plan(10, 8, r)
+    A_dev = torch.from_numpy(A).float().to(DEV)
+    p_dev = torch.from_numpy(p32).float().to(DEV)
+    loss, _, g = pl.loss_grad(A_dev, p_dev, "bf16")
+    loss_ref, resid = o.residual(o.coeffs(A16), p32)
+    g_ref = o.grad_from_resid(A16, resid)
+    u = 2.0 ** -23
+    c_abs = o.coeffs(absA)
+    dnorm = (r / 16 + 64) * u * np.linalg.norm(c_abs)
+    assert abs(loss.item() - loss_ref) <= np.linalg.norm(resid) * dnorm + 0.5 * dnorm ** 2 + 1e-6 * loss_ref
+    dc = (r + o.N) * u * c_abs
+    dh = dc + 2.0 ** -8 * (np.abs(resid) + dc)
+    bound = o.grad_from_resid(absA, dh) + o.N * u * o.grad_from_resid(absA, np.abs(resid) + dh) + 1e-30
+    assert np.all(np.abs(g.cpu().numpy() - g_ref) <= bound)
+    lr = 1e-4
+    opt = Optimizer(pl, A_dev, prec="bf16", optimizer="gd", lr=lr)
+    opt.step(p_dev)
+    want = A.astype(np.float32).astype(np.float64) - lr * g_ref
+    assert np.all(np.abs(A_dev.double().cpu().numpy() - want) <= lr * bound + 4 * 2.0 ** -24 * np.abs(want) + 1e-30)
+
+
 @pytest.mark.parametrize("n,two_d,r", [(6, 8, 210), (7, 8, 130), (9, 6, 700)])
 def test_fused_bf16_gd_steps(n, two_d, r):
     o, A, p = problem(n, two_d, r)
