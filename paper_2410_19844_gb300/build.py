@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsos_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["plan.cpp", "timing.cpp", "kernels_simt.cu", "kernels_tc.cu", "kernels_tc2.cu", "api.cu", "solve.cpp", "group.cu", "layer.cu", "slices.cu"]
+SOURCES = ["plan.cpp", "timing.cpp", "kernels_simt.cu", "kernels_tc.cu", "kernels_tc2.cu", "api.cu", "solve.cpp", "group.cu", "layer.cu", "slices.cu", "h16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE]

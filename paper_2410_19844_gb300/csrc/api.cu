@@ -38,7 +38,7 @@ int pass_tc64(sos_plan_s* p, const double* A, const double* pv, float* g32, void
     if (!g32) return SOS_OK;
     float* r32 = at<float>(ws, w.resid32);
     SOS_CHECK(launch_convert<double, float>(resid, r32, p->M, st));
-    SOS_CHECK(launch_build_h16(p, r32, at<char>(ws, w.h16), st));
+    SOS_CHECK(launch_build_h16(p, r32, at<char>(ws, w.h16), status, st));
     return launch_tc_adjoint_pair(p, at<char>(ws, w.h16), at<char>(ws, w.a16), g32, status, st);
 }
 
@@ -94,7 +94,7 @@ int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad
         return launch_simt_adjoint<float>(p, static_cast<const float*>(A), resid, static_cast<float*>(grad), 1,
                                           st);
     void* h16 = at<char>(ws, w.h16);
-    SOS_CHECK(launch_build_h16(p, resid, h16, st));
+    SOS_CHECK(launch_build_h16(p, resid, h16, status, st));
     return use_cta_pairs()
                ? launch_tc_adjoint_pair(p, h16, at<char>(ws, w.a16), static_cast<float*>(grad), status, st)
                : launch_tc_adjoint(p, h16, at<char>(ws, w.a16), static_cast<float*>(grad), status, st);
@@ -234,7 +234,7 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         SOS_CHECK(launch_residual<float>(p, c, static_cast<const float*>(pv), resid, L, at<double>(ws, w.partials),
                                          status, 1, st));
         void* h16 = at<char>(ws, w.h16);
-        SOS_CHECK(launch_build_h16(p, resid, h16, st));
+        SOS_CHECK(launch_build_h16(p, resid, h16, status, st));
         auto adj = use_cta_pairs() ? launch_tc_adjoint_update_pair : launch_tc_adjoint_update;
         SOS_CHECK(adj(p, h16, a16_cur, a16_next, static_cast<float*>(s->A), static_cast<float*>(s->m),
                       static_cast<float*>(s->v), o->optimizer, t, o->lr, o->beta1, o->beta2, o->eps, status, st));

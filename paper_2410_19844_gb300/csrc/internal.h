@@ -163,7 +163,8 @@ int launch_residual(const sos_plan_s* plan, const T* c, const T* p, T* resid, do
 template <typename T>
 int launch_simt_adjoint(const sos_plan_s* plan, const T* A, const T* resid, T* grad,
                         int64_t batch, cudaStream_t st, bool fp32_contraction = false);
-int launch_build_h16(const sos_plan_s* plan, const float* resid, void* h16, cudaStream_t st);
+// H(resid) in bf16 (h16.cu); a timed-out wait sets *status to SOS_E_TIMEOUT.
+int launch_build_h16(const sos_plan_s* plan, const float* resid, void* h16, int32_t* status, cudaStream_t st);
 template <typename T>
 int launch_update(int64_t N, int64_t r, T* A, T* m, T* v, const T* grad, int optimizer,
                   int64_t t, double lr, double b1, double b2, double eps, void* a16,

@@ -449,73 +449,6 @@ simt_adjoint128_kernel(const T* __restrict__ A, const T* __restrict__ resid, con
     }
 }
 
-// ---- H(r) in bf16 for the tensor-core adjoint ----------------------------------------
-// H is symmetric (idx(a, b) = idx(b, a)), so each block reads the index table
-// and gathers the residual for one 64 x 64 tile on or above the diagonal and
-// writes both that tile and its transpose (through shared memory, so both
-// writes are row-contiguous).
-
-__global__ void __launch_bounds__(kThreads)
-build_h16_kernel(const float* __restrict__ resid, const int32_t* __restrict__ idx, int64_t ld_idx, int64_t N,
-                 __nv_bfloat16* __restrict__ h, int64_t ldh) {
-    const int I = blockIdx.y, J = blockIdx.x;
-    if (J < I) return;
-    __shared__ float tileT[64][65];
-    const int64_t a0 = (int64_t)I * 64, b0 = (int64_t)J * 64;
-    const int cc = (threadIdx.x & 15) * 4;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int rr = (threadIdx.x >> 4) + 16 * k;
-        const int64_t a = a0 + rr, b = b0 + cc;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (a < N) {
-            const int32_t* irow = idx + a * ld_idx + b;
-            __nv_bfloat16* hrow = h + a * ldh + b;
-            if (b + 4 <= N) {
-                const int4 g = *reinterpret_cast<const int4*>(irow);
-                v[0] = resid[g.x];
-                v[1] = resid[g.y];
-                v[2] = resid[g.z];
-                v[3] = resid[g.w];
-                __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
-                __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
-                uint2 out;
-                out.x = *reinterpret_cast<uint32_t*>(&lo);
-                out.y = *reinterpret_cast<uint32_t*>(&hi);
-                *reinterpret_cast<uint2*>(hrow) = out;
-            } else {
-                for (int j = 0; j < 4 && b + j < N; ++j) {
-                    v[j] = resid[irow[j]];
-                    hrow[j] = __float2bfloat16_rn(v[j]);
-                }
-            }
-        }
-        if (I != J) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) tileT[cc + j][rr] = v[j];
-        }
-    }
-    if (I == J) return;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int rr = (threadIdx.x >> 4) + 16 * k;
-        const int64_t b = b0 + rr, a = a0 + cc;      // row b of H, columns a .. a+3
-        if (b >= N) continue;
-        __nv_bfloat16* hrow = h + b * ldh + a;
-        if (a + 4 <= N) {
-            __nv_bfloat162 lo = __floats2bfloat162_rn(tileT[rr][cc], tileT[rr][cc + 1]);
-            __nv_bfloat162 hi = __floats2bfloat162_rn(tileT[rr][cc + 2], tileT[rr][cc + 3]);
-            uint2 out;
-            out.x = *reinterpret_cast<uint32_t*>(&lo);
-            out.y = *reinterpret_cast<uint32_t*>(&hi);
-            *reinterpret_cast<uint2*>(hrow) = out;
-        } else {
-            for (int j = 0; j < 4 && a + j < N; ++j) hrow[j] = __float2bfloat16_rn(tileT[rr][cc + j]);
-        }
-    }
-}
-
 // ---- optimiser update ---------------------------------------------------------------
 
 template <typename T>
@@ -669,19 +602,6 @@ int launch_simt_adjoint(const sos_plan_s* p, const T* A, const T* resid, T* grad
         else
             simt_adjoint_kernel<T, T><<<grid, kThreads, 0, st>>>(A, resid, p->dev.idx, p->ld_idx, p->N, p->r, grad,
                                                                  p->N * p->r, p->M);
-    }
-    SOS_CUDA(cudaGetLastError());
-    return SOS_OK;
-}
-
-int launch_build_h16(const sos_plan_s* p, const float* resid, void* h16, cudaStream_t st) {
-    const int64_t T = ceil_div(p->N, 64);
-    if (T > 65535) return fail(SOS_E_UNSUPPORTED, "build_h16: too many tiles");
-    dim3 grid((unsigned)T, (unsigned)T);
-    {
-        KernelScope ks_("build_h16", st);
-        build_h16_kernel<<<grid, kThreads, 0, st>>>(resid, p->dev.idx, p->ld_idx, p->N, (__nv_bfloat16*)h16,
-                                                    p->ld16h);
     }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
