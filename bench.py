@@ -150,7 +150,16 @@ def committed_traffic(kernel: str):
 
 # -- CPU oracle sample --------------------------------------------------------------
 
-def oracle_sample(w, widths=(8, 16), reps=2, seed=0):
+def linear_fit(t_small, c_small, t_big, c_big, cols):
+    """Extrapolates a per-iteration time that costs a + b * columns from two
+    column widths to `cols` columns; (a, b, t(cols)).  The callers take the
+    widths far enough apart that timing noise cannot flatten the slope."""
+    b = max(t_big - t_small, 0.0) / (c_big - c_small)
+    a = max(t_small - b * c_small, 0.0)
+    return a, b, a + b * cols
+
+
+def oracle_sample(w, widths=(8, 32), reps=2, seed=0):
     """Times one oracle GD iteration (coefficients, residual, gradient, update) on
     column slices of A and extrapolates linearly in the number of columns: the
     oracle's cost is a + b * columns (pair-table lookups plus per-column dot
@@ -176,10 +185,7 @@ def oracle_sample(w, widths=(8, 16), reps=2, seed=0):
             best = dt if best is None else min(best, dt)
         times[cols] = best
     (c1, t1), (c2, t2) = sorted(times.items())
-    t2 = max(t2, t1)
-    b = (t2 - t1) / (c2 - c1)
-    a = max(t1 - b * c1, 0.0)
-    t_full = a + b * w.cols
+    a, b, t_full = linear_fit(t1, c1, t2, c2, w.cols)
     desc = (f"oracle GD iteration on column slices of width {list(times)} of the {w.N} x {w.cols} A "
             f"(full M = {w.M}), best of {reps}: {', '.join(f'{k} cols {v:.3f} s' for k, v in times.items())}; "
             f"fit t = {a:.3f} s + {b:.4f} s/col, extrapolated to {w.cols} cols = {t_full:.1f} s/iter; "
@@ -218,10 +224,7 @@ def blas_sample(w, widths=(256, 512), reps=2, seed=0):
             best = dt if best is None else min(best, dt)
         times[cols] = best
     (c1, t1), (c2, t2) = sorted(times.items())
-    t2 = max(t2, t1)
-    b = (t2 - t1) / (c2 - c1)
-    a = max(t1 - b * c1, 0.0)
-    t_full = a + b * w.cols
+    a, b, t_full = linear_fit(t1, c1, t2, c2, w.cols)
     desc = (f"torch CPU fp32 GD iteration (A A^T, index_add into c, gather H, 2 H A) on column slices of "
             f"width {list(times)}, best of {reps}: {', '.join(f'{k} cols {v:.3f} s' for k, v in times.items())}; "
             f"fit t = {a:.3f} s + {b:.5f} s/col, extrapolated to {w.cols} cols = {t_full:.1f} s/iter; "
@@ -250,26 +253,30 @@ def run_reference(args):
         loss, grad, _c = o.loss_grad(A, p)
         o.gd_step(A, grad, 1e-7)
 
-    # a second width, once, gives the column-independent part of the cost
-    A2 = sos_inputs.normal_matrix(w.N, 2 * cols, 1, sigma=w.init_sigma)
+    # a fourfold width, once, gives the per-column part of the cost
+    wide = 4 * cols
+    A2 = sos_inputs.normal_matrix(w.N, wide, 1, sigma=w.init_sigma)
+
+    def step_wide():
+        loss, grad, _c = o.loss_grad(A2, p)
+        o.gd_step(A2, grad, 1e-7)
+
     for _ in range(args.warmup):
         step()
     t_2 = None
     for _ in range(2):
         t_a = time.perf_counter()
-        o.loss_grad(A2, p)
+        step_wide()
         dt = time.perf_counter() - t_a
         t_2 = dt if t_2 is None else min(t_2, dt)
     t_a = time.perf_counter()
     for _ in range(args.steps):
         step()
     t_1 = (time.perf_counter() - t_a) / args.steps
-    b = max((t_2 - t_1) / cols, t_1 / cols * 0.5)
-    a = max(t_1 - b * cols, 0.0)
-    t_full = a + b * w.cols
+    a, b, t_full = linear_fit(t_1, cols, t_2, wide, w.cols)
     value = 1.0 / t_full
     sample = (f"each step: one oracle GD iteration on a {w.N} x {cols} column slice of A (full M = {w.M}); "
-              f"{t_1:.3f} s/step, {2 * cols} columns {t_2:.3f} s; cost a + b*cols with a = {a:.3f} s, "
+              f"{t_1:.3f} s/step, {wide} columns {t_2:.3f} s; cost a + b*cols with a = {a:.3f} s, "
               f"b = {b:.4f} s/col, extrapolated to {w.cols} columns = {t_full:.1f} s/iter; "
               f"table setup {setup:.1f} s untimed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
