@@ -117,7 +117,7 @@ build_h16_tma_kernel(const __grid_constant__ CUtensorMap map_idx, const __grid_c
         const int s = it % IDX_STAGES;
         const int32_t* sidx = reinterpret_cast<const int32_t*>(base + s * IDX_BYTES);
         if (threadIdx.x == 0) {
-            // tile it + IDX_STAGES - 1 goes to the block that tile it - 1 used
+            // tile it + IDX_STAGES - 1 goes to the index buffer that tile it - 1 used
             const int64_t tn = t + (int64_t)(IDX_STAGES - 1) * gridDim.x;
             if (tn < total) {
                 const int sn = (it + IDX_STAGES - 1) % IDX_STAGES;
