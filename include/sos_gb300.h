@@ -252,8 +252,13 @@ int sos_layer_loss_grad(sos_plan_t plan, int prec, int m, const void* B, const v
 
 /* Optimiser state of the network, all dev and caller-owned: B, A1 updated in
  * place; mB, vB (k x nf*m) and mA1, vA1 (m x nf) zero before the first Adam
- * step; t = steps already taken.  flags: 0, or SOS_LAYER_FIXED_A1 to keep A1
- * as it is (the paper's A = I comparison; mA1, vA1 may then be NULL). */
+ * step; t = steps already taken.  flags: SOS_LAYER_FIXED_A1 keeps A1 as it is
+ * (the paper's A = I comparison; mA1, vA1 may then be NULL).
+ * SOS_LAYER_BF16_CURRENT is set by a BF16 sos_layer_step whose layer GEMMs ran
+ * on the tensor cores: its update also wrote the bf16 copy of the new B into
+ * the workspace, and the next such step with the same workspace reuses it
+ * instead of casting B.  The library clears it after any other step; clear it
+ * yourself when B changes outside the library or the workspace changes. */
 typedef struct {
     void* B;
     void* mB;
@@ -267,6 +272,7 @@ typedef struct {
 } sos_layer_state;
 
 #define SOS_LAYER_FIXED_A1 1
+#define SOS_LAYER_BF16_CURRENT 2
 
 /* One iteration: loss and gradients at (B, A1), then the update of B (and A1).
  * opts as for sos_step (SOS_STEP_FP32_ADJOINT applies to the core adjoint of

@@ -58,6 +58,7 @@ class sos_layer_state(ctypes.Structure):
 
 
 SOS_LAYER_FIXED_A1 = 1
+SOS_LAYER_BF16_CURRENT = 2
 
 
 class sos_state(ctypes.Structure):

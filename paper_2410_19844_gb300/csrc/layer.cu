@@ -146,31 +146,71 @@ __global__ void split_sum_kernel(const T* __restrict__ part, int splits, int64_t
     }
 }
 
+constexpr int kTT = 32;   // tile edge of the expand and scatter transposes (blocks of 32 x 8 threads)
+
 // A_hat[a][kk] = P_kk[i][j] + P_kk[j][i] (i < j) or P_kk[i][i], (i, j) = pairs[a].
+// A block takes 32 monomials a by 32 outputs kk through shared memory, so that
+// the reads walk a (consecutive pairs are mostly consecutive j in one row of
+// P_kk) and the writes walk kk along a row of A_hat.  Grid (ceil(N / 32),
+// ceil(k / 32)).
 template <typename T>
-__global__ void form_expand_kernel(const T* __restrict__ P, const int2* __restrict__ pairs, int64_t N, int64_t k,
-                                   int nf, T* __restrict__ Ahat) {
-    const int64_t count = N * k;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = e / k, kk = e % k;
-        const int2 ij = pairs[a];
-        const T* Pk = P + kk * nf * nf;
-        T v = Pk[ij.x * nf + ij.y];
-        if (ij.x != ij.y) v += Pk[ij.y * nf + ij.x];
-        Ahat[e] = v;
+__global__ void __launch_bounds__(256) form_expand_kernel(const T* __restrict__ P, const int2* __restrict__ pairs,
+                                                          int64_t N, int64_t k, int nf, T* __restrict__ Ahat) {
+    __shared__ T tile[kTT][kTT + 1];
+    const int64_t a0 = (int64_t)blockIdx.x * kTT, kk0 = (int64_t)blockIdx.y * kTT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t nf2 = (int64_t)nf * nf, a = a0 + tx;
+    const int2 ij = a < N ? pairs[a] : make_int2(0, 0);
+#pragma unroll
+    for (int r = 0; r < kTT; r += 8) {
+        const int64_t kk = kk0 + ty + r;
+        T v = T(0);
+        if (a < N && kk < k) {
+            const T* Pk = P + kk * nf2;
+            v = Pk[ij.x * nf + ij.y];
+            if (ij.x != ij.y) v += Pk[ij.y * nf + ij.x];
+        }
+        tile[ty + r][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kTT; r += 8) {
+        const int64_t row = a0 + ty + r, kk = kk0 + tx;
+        if (row < N && kk < k) Ahat[row * k + kk] = tile[tx][ty + r];
     }
 }
 
 // S_kk[i][j] = G[rows[i][j]][kk] for every (i, j): the gradient with respect to
-// P_kk, symmetric because x_i x_j and x_j x_i are one monomial.
+// P_kk, symmetric because x_i x_j and x_j x_i are one monomial.  When S16 is
+// not NULL the same values also go to S16 in bf16, row kk * nf + i of stride
+// ld (the tensor-core operand).  A block takes 32 entries ij by 32 outputs kk
+// through shared memory: the reads walk kk along a row of G, the writes walk
+// ij.  Grid (ceil(nf^2 / 32), ceil(k / 32)).
 template <typename T>
-__global__ void form_scatter_kernel(const T* __restrict__ G, const int32_t* __restrict__ rows, int64_t k, int nf,
-                                    T* __restrict__ S) {
-    const int64_t count = k * nf * nf;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t kk = e / ((int64_t)nf * nf);
-        const int ij = (int)(e % ((int64_t)nf * nf));
-        S[e] = G[(int64_t)rows[ij] * k + kk];
+__global__ void __launch_bounds__(256) form_scatter_kernel(const T* __restrict__ G, const int32_t* __restrict__ rows,
+                                                           int64_t k, int nf, T* __restrict__ S,
+                                                           __nv_bfloat16* __restrict__ S16, int64_t ld) {
+    __shared__ T tile[kTT][kTT + 1];
+    const int64_t nf2 = (int64_t)nf * nf;
+    const int64_t ij0 = (int64_t)blockIdx.x * kTT, kk0 = (int64_t)blockIdx.y * kTT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int r = 0; r < kTT; r += 8) {
+        const int64_t ij = ij0 + ty + r, kk = kk0 + tx;
+        tile[ty + r][tx] = (ij < nf2 && kk < k) ? G[(int64_t)rows[ij] * k + kk] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kTT; r += 8) {
+        const int64_t kk = kk0 + ty + r, ij = ij0 + tx;
+        if (ij < nf2 && kk < k) {
+            const T v = tile[tx][ty + r];
+            S[kk * nf2 + ij] = v;
+            if (S16) {
+                const int64_t i = ij / nf, j = ij - i * nf;
+                S16[(kk * nf + i) * ld + j] = __float2bfloat16_rn((float)v);
+            }
+        }
     }
 }
 
@@ -181,18 +221,6 @@ __global__ void cast_rows_bf16_kernel(const float* __restrict__ x, int64_t rows,
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / cols, j = e - i * cols;
         y[i * ld + j] = __float2bfloat16_rn(x[e]);
-    }
-}
-
-// S_kk[i][j] = G[rows[i][j]][kk] as bf16 into rows of ld (the tensor-core operand).
-__global__ void form_scatter_bf16_kernel(const float* __restrict__ G, const int32_t* __restrict__ rows, int64_t k,
-                                         int nf, __nv_bfloat16* __restrict__ S, int64_t ld) {
-    const int64_t count = k * nf * nf;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / nf;            // row kk * nf + i
-        const int j = (int)(e - r * nf), i = (int)(r % nf);
-        const int64_t kk = r / nf;
-        S[r * ld + j] = __float2bfloat16_rn(G[(int64_t)rows[i * nf + j] * k + kk]);
     }
 }
 
@@ -340,7 +368,8 @@ int launch_gemm(int64_t M, int64_t Ncol, int64_t K, int64_t kchunk, int splits, 
 
 // P_k = M_k A1 for every k, then A_hat.
 template <typename T>
-int expand(sos_plan_s* p, int m, const T* B, const T* A1, T* Ahat, const LayerLayout& w, void* ws, cudaStream_t st) {
+int expand(sos_plan_s* p, int m, const T* B, const T* A1, T* Ahat, const LayerLayout& w, void* ws, cudaStream_t st,
+           bool b16_current = false) {
     const int64_t nf = p->n + 1, k = p->r;
     T* P = at<T>(ws, w.P);
     bool done = false;
@@ -351,7 +380,8 @@ int expand(sos_plan_s* p, int m, const T* B, const T* A1, T* Ahat, const LayerLa
             int2* tiles = at<int2>(ws, w.tilesP);
             {
                 KernelScope ks_("layer_cast", st);
-                cast_rows_bf16_kernel<<<grid_for(k * nf * m), 256, 0, st>>>(B, k * nf, m, B16, w.ldm);
+                if (!b16_current)   // else the previous step's update left the bf16 copy of B
+                    cast_rows_bf16_kernel<<<grid_for(k * nf * m), 256, 0, st>>>(B, k * nf, m, B16, w.ldm);
                 cast_rows_bf16_kernel<<<grid_for((int64_t)m * nf), 256, 0, st>>>(A1, m, nf, A116, w.ldnf);
                 tile_grid_kernel<<<grid_for(w.ntP), 256, 0, st>>>((int)ceil_div(k * nf, 256), (int)ceil_div(nf, 256),
                                                                  tiles);
@@ -366,7 +396,9 @@ int expand(sos_plan_s* p, int m, const T* B, const T* A1, T* Ahat, const LayerLa
         SOS_CHECK(launch_gemm<T>(k * nf, nf, m, m, 1, B, m, 1, A1, nf, 1, P, nf, 0, st));
     {
         KernelScope ks_("layer_expand", st);
-        form_expand_kernel<T><<<grid_for(p->N * k), 256, 0, st>>>(P, p->dev.form_pairs, p->N, k, (int)nf, Ahat);
+        if (ceil_div(k, kTT) > 65535) return fail(SOS_E_UNSUPPORTED, "first layer: k too large for the expand grid");
+        const dim3 grid((unsigned)ceil_div(p->N, kTT), (unsigned)ceil_div(k, kTT));
+        form_expand_kernel<T><<<grid, dim3(kTT, 8), 0, st>>>(P, p->dev.form_pairs, p->N, k, (int)nf, Ahat);
     }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
@@ -378,21 +410,24 @@ int pull_back(sos_plan_s* p, int m, const T* B, const T* A1, const T* gAhat, T* 
               void* ws, cudaStream_t st) {
     const int64_t nf = p->n + 1, k = p->r;
     T* S = at<T>(ws, w.P);
+    // BF16 steps take dL/dB on the tensor cores from a bf16 copy of S, written by the same scatter
+    const bool tc_gB = std::is_same<T, float>::value && w.tc && gB;
     {
         KernelScope ks_("layer_scatter", st);
-        form_scatter_kernel<T><<<grid_for(k * nf * nf), 256, 0, st>>>(gAhat, p->dev.form_rows, k, (int)nf, S);
+        if (ceil_div(k, kTT) > 65535) return fail(SOS_E_UNSUPPORTED, "first layer: k too large for the scatter grid");
+        const dim3 grid((unsigned)ceil_div(nf * nf, kTT), (unsigned)ceil_div(k, kTT));
+        form_scatter_kernel<T><<<grid, dim3(kTT, 8), 0, st>>>(gAhat, p->dev.form_rows, k, (int)nf, S,
+                                                              tc_gB ? at<__nv_bfloat16>(ws, w.S16) : nullptr, w.ldnf);
     }
     SOS_CUDA(cudaGetLastError());
     bool gb_done = false;
     if constexpr (std::is_same<T, float>::value) {
-        if (w.tc && gB) {   // BF16 step: S in bf16, then (k nf) x nf times (m x nf)^T on tensor cores
+        if (tc_gB) {   // (k nf) x nf times (m x nf)^T on tensor cores
             auto* S16 = at<__nv_bfloat16>(ws, w.S16);
             auto* A116 = at<__nv_bfloat16>(ws, w.A116);   // cast by expand() in this pass
             int2* tiles = at<int2>(ws, w.tilesG);
             {
                 KernelScope ks_("layer_scatter", st);
-                form_scatter_bf16_kernel<<<grid_for(k * nf * nf), 256, 0, st>>>(gAhat, p->dev.form_rows, k, (int)nf,
-                                                                               S16, w.ldnf);
                 tile_grid_kernel<<<grid_for(w.ntG), 256, 0, st>>>((int)ceil_div(k * nf, 256), (int)ceil_div(m, 256),
                                                                  tiles);
             }
@@ -416,11 +451,11 @@ int pull_back(sos_plan_s* p, int m, const T* B, const T* A1, const T* gAhat, T* 
 
 template <typename T>
 int layer_loss_grad(sos_plan_s* p, int prec, int m, const void* B, const void* A1, const void* pv, void* gB, void* gA1,
-                    void* loss, void* ws, cudaStream_t st, bool fp32_contraction) {
+                    void* loss, void* ws, cudaStream_t st, bool fp32_contraction, bool b16_current = false) {
     const LayerLayout w = layer_layout(p, prec, m);
     T* Ahat = at<T>(ws, w.Ahat);
     T* gAhat = (gB || gA1) ? at<T>(ws, w.gAhat) : nullptr;
-    SOS_CHECK(expand<T>(p, m, static_cast<const T*>(B), static_cast<const T*>(A1), Ahat, w, ws, st));
+    SOS_CHECK(expand<T>(p, m, static_cast<const T*>(B), static_cast<const T*>(A1), Ahat, w, ws, st, b16_current));
     SOS_CHECK(core_loss_grad(p, prec, Ahat, pv, gAhat, loss, at<char>(ws, w.core), st, fp32_contraction));
     if (gAhat)
         SOS_CHECK(pull_back<T>(p, m, static_cast<const T*>(B), static_cast<const T*>(A1), gAhat, static_cast<T*>(gB),
@@ -478,7 +513,8 @@ int sos_layer_step(sos_plan_t p, int prec, int m, sos_layer_state* s, const void
     if (o->optimizer == SOS_ADAM && (!s->mB || !s->vB || (!fixed && (!s->mA1 || !s->vA1))))
         return fail(SOS_E_INVALID, "sos_layer_step: Adam needs m and v for every trained matrix");
     if (o->flags & ~SOS_STEP_FP32_ADJOINT) return fail(SOS_E_INVALID, "sos_layer_step: unknown flags");
-    if (s->flags & ~SOS_LAYER_FIXED_A1) return fail(SOS_E_INVALID, "sos_layer_step: unknown state flags");
+    if (s->flags & ~(SOS_LAYER_FIXED_A1 | SOS_LAYER_BF16_CURRENT))
+        return fail(SOS_E_INVALID, "sos_layer_step: unknown state flags");
     SOS_CHECK(ensure_form_tables(p));
     cudaStream_t st = (cudaStream_t)stream;
     const LayerLayout w = layer_layout(p, prec, m);
@@ -498,15 +534,22 @@ int sos_layer_step(sos_plan_t p, int prec, int m, sos_layer_state* s, const void
     } else {
         float* gB = at<float>(ws, w.gB);
         float* gA1 = fixed ? nullptr : at<float>(ws, w.gA1);
-        SOS_CHECK(layer_loss_grad<float>(p, prec, m, s->B, s->A1, pv, gB, gA1, loss, ws, st, false));
-        SOS_CHECK(launch_update<float>(k, nf * m, static_cast<float*>(s->B), static_cast<float*>(s->mB),
+        const bool b16 = w.tc != 0;   // BF16 step with the layer's GEMMs on tensor cores
+        SOS_CHECK(layer_loss_grad<float>(p, prec, m, s->B, s->A1, pv, gB, gA1, loss, ws, st, false,
+                                         b16 && (s->flags & SOS_LAYER_BF16_CURRENT)));
+        // B as (k nf) x m, so that the update also writes the next step's bf16 copy in its padded rows
+        SOS_CHECK(launch_update<float>(k * nf, m, static_cast<float*>(s->B), static_cast<float*>(s->mB),
                                        static_cast<float*>(s->vB), gB, o->optimizer, t, o->lr, o->beta1, o->beta2,
-                                       o->eps, nullptr, 0, st));
+                                       o->eps, b16 ? at<char>(ws, w.B16) : nullptr, b16 ? w.ldm : 0, st));
         if (!fixed)
             SOS_CHECK(launch_update<float>(m, nf, static_cast<float*>(s->A1), static_cast<float*>(s->mA1),
                                            static_cast<float*>(s->vA1), gA1, o->optimizer, t, o->lr, o->beta1,
                                            o->beta2, o->eps, nullptr, 0, st));
     }
+    if (prec == SOS_BF16 && w.tc)
+        s->flags |= SOS_LAYER_BF16_CURRENT;
+    else
+        s->flags &= ~SOS_LAYER_BF16_CURRENT;
     s->t = t;
     return SOS_OK;
 }

@@ -266,6 +266,11 @@ class LayerOptimizer:
     def t(self) -> int:
         return self.state.t
 
+    def params_changed(self) -> None:
+        """Call after changing B in place outside step(): the next BF16 step then
+        casts B again instead of reusing the bf16 copy its update left."""
+        self.state.flags &= ~L.SOS_LAYER_BF16_CURRENT
+
     def step(self, p: torch.Tensor) -> torch.Tensor:
         """One iteration; returns the device tensor {loss before the step, ||p||^2}."""
         L.sos_layer_step(self.layer.plan.handle, self.prec, self.layer.m, self.state, _ptr(p), self.opts,

@@ -131,6 +131,41 @@ def test_layer_gd_step_fp32():
     assert rel(A1d.cpu().numpy() - A132, -lr * gA1) < 1e-3
 
 
+def test_layer_bf16_steps_reuse_the_updated_bf16_copy():
+    # nf, m >= 64: the layer's GEMMs run on the tensor cores, and each BF16 step's
+    # update writes the bf16 copy of the new B that the next step reads
+    # (SOS_LAYER_BF16_CURRENT).  The loss a step reports is the loss at the B
+    # it starts from: it must equal a fresh evaluation at that B, which casts B
+    # itself (the core forward's float atomics allow 1e-5).
+    nf, m, k = 64, 70, 20
+    _, B, A1, p = case(nf, m, k, seed=8)
+    lay = Layer(Plan(nf - 1, 4, k), m)
+    Bd, A1d = torch.from_numpy(B).float().cuda(), torch.from_numpy(A1).float().cuda()
+    pd = torch.from_numpy(p).float().cuda()
+    opt = LayerOptimizer(lay, Bd, A1d, prec="bf16", optimizer="gd", lr=1e-9)   # about 0.5% less loss a step
+    assert not opt.state.flags & L.SOS_LAYER_BF16_CURRENT
+    first = opt.step(pd)[0].item()
+    assert opt.state.flags & L.SOS_LAYER_BF16_CURRENT
+    probe = Layer(Plan(nf - 1, 4, k), m)
+    for _ in range(3):
+        fresh = probe.loss_grad(Bd.clone(), A1d.clone(), pd, "bf16", want_grad=False)[0].item()
+        assert abs(fresh - first) > 1e-3 * first          # the step moved B
+        got = opt.step(pd)[0].item()
+        assert abs(got - fresh) <= 1e-5 * fresh
+        first = got
+    # B changed outside the library: params_changed() makes the next step cast it again
+    Bd.mul_(1.05)
+    opt.params_changed()
+    fresh = probe.loss_grad(Bd.clone(), A1d.clone(), pd, "bf16", want_grad=False)[0].item()
+    got = opt.step(pd)[0].item()
+    assert abs(got - fresh) <= 1e-5 * fresh
+    # an FP32 step on the same state leaves no claim on the bf16 copy
+    opt32 = LayerOptimizer(lay, Bd, A1d, prec="fp32", optimizer="gd", lr=1e-9)
+    opt32.state.flags = opt.state.flags
+    opt32.step(pd)
+    assert not opt32.state.flags & L.SOS_LAYER_BF16_CURRENT
+
+
 def test_layer_rejects_bad_arguments():
     with pytest.raises(ValueError):
         Layer(Plan(3, 6), 4)
