@@ -30,7 +30,11 @@ namespace tc {
 constexpr int STAGE_LD = 33;
 
 // Forward: c[idx(a, b)] += w G_ab for b >= a (w = 1 on the diagonal, 2 above).
-// All 32 index loads are issued before the first atomic, so they overlap.
+// The warp walks the 32 x 32 block in 4 x 8 patches (lane = 8 dr + dc: row
+// 4 (t / 4) + dr, column 8 (t % 4) + dc at step t): entries (a, b) and
+// (a + 1, b - 1) often share the monomial a + b, so a compact patch's 32
+// atomics touch about half the 32-byte sectors of c that one row's do.  All
+// 32 index loads are issued before the first atomic, so they overlap.
 struct SegmentSumEpilogue {
     static constexpr const char* kName = "tc_forward";
     static constexpr bool kSegmented = false;
@@ -41,20 +45,19 @@ struct SegmentSumEpilogue {
 
     __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
         if (a0 >= N || b0 >= N || b0 + 31 < a0) return;
-        const int b = b0 + lane;
-        if (b >= N) return;
-        const int32_t* col = idx + (int64_t)a0 * ld_idx + b;
+        const int dr = lane >> 3, dc = lane & 7;
         int32_t g[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int a = a0 + i;
-            g[i] = (a < N && a <= b) ? __ldg(col + (int64_t)i * ld_idx) : -1;
+        for (int t = 0; t < 32; ++t) {
+            const int a = a0 + 4 * (t >> 2) + dr, b = b0 + 8 * (t & 3) + dc;
+            g[t] = (a < N && b < N && a <= b) ? __ldg(idx + (int64_t)a * ld_idx + b) : -1;
         }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            if (g[i] >= 0) {
-                const float v = stage[i * STAGE_LD + lane];
-                atomicAdd(c + g[i], a0 + i == b ? v : 2.0f * v);
+        for (int t = 0; t < 32; ++t) {
+            if (g[t] >= 0) {
+                const int i = 4 * (t >> 2) + dr, j = 8 * (t & 3) + dc;
+                const float v = stage[i * STAGE_LD + j];
+                atomicAdd(c + g[t], a0 + i == b0 + j ? v : 2.0f * v);
             }
         }
     }
