@@ -93,6 +93,10 @@ typedef enum {
  * fit (M must stay below 2^31). */
 int sos_plan_create(int n, int two_d, int64_t r, sos_plan_t* out);
 
+/* The same call under its short name: sos_plan(n, 2d, r) builds the
+ * monomial tables of Sec. 1.1 and the index table idx(a + b) of Eq. 1. */
+int sos_plan(int n, int two_d, int64_t r, sos_plan_t* out);
+
 /* Frees the plan, its host tables and (with its device current) its device
  * tables.  NULL is accepted. */
 int sos_plan_destroy(sos_plan_t plan);
@@ -109,6 +113,13 @@ int sos_plan_monomials(sos_plan_t plan, int which, uint8_t* exps);
  * index table of the Gram identity (Eq. 1): c_g = sum_{a+b=g} (A A^T)_ab.
  * host N x N int32.  SOS_E_NOMEM if N*N exceeds 2^31 entries. */
 int sos_plan_idx(sos_plan_t plan, int32_t* idx);
+
+/* Test hook: copies rows [row0, row0 + rows) of the index table the kernels
+ * read on the current device (the same idx(a, b) = position of x^a x^b as
+ * sos_plan_idx, Eq. 1, but built on the device from the closed-form rank)
+ * into host idx, N entries per row (host rows x N int32).  Uploads the plan
+ * first when needed; synchronous.  SOS_E_INVALID for rows outside 0 .. N-1. */
+int sos_plan_device_idx(sos_plan_t plan, int64_t row0, int64_t rows, int32_t* idx);
 
 /* Bytes of device workspace that sos_coeffs / sos_loss_grad / sos_step need
  * for this plan and precision.  Callers allocate it (any 256-byte aligned
@@ -143,20 +154,22 @@ int sos_loss_grad_batched(sos_plan_t plan, int prec, int64_t batch, const void* 
                           const void* p, void* grad, void* loss, void* workspace,
                           void* stream);
 
-/* The loss of Eq. 2 from coefficients the caller already has, for callers
- * that cannot allocate device memory when they call (a host framework that
- * only hands a library the buffers it allocated itself, or a loop that runs
- * under a fixed memory budget).  The paper has no counterpart: it is the
- * residual and loss reduction of sos_loss_grad with its scratch (status word,
- * ticket counters, per-block partial sums) kept in a fixed 1 MiB array that
- * the library holds on every GPU that loads it, until the process exits.
- * This entry point calls no allocator.
+/* The loss 1/2 ||c - p||^2 from coefficients the caller already has, for
+ * callers that cannot allocate device memory when they call: a host framework
+ * that only hands a library buffers it allocated itself, or a loop held to a
+ * fixed memory budget, where an allocation inside the call could fail or
+ * synchronise the device.  The paper has no counterpart to this entry point.
+ * It runs the residual and loss reduction of sos_loss_grad with that
+ * kernel's scratch (status word, ticket counters, per-block partial sums)
+ * kept in a fixed 1 MiB array that the library holds on every GPU that loads
+ * it, until the process exits.  It calls no allocator.
  *   prec: SOS_FP32 (float c, p, resid) or SOS_FP64 (double);
  *   c, p: dev batch x M; resid: dev batch x M (c - p) or NULL;
  *   loss: dev double[batch][2] = {1/2 ||c - p||^2, ||p||^2} per problem.
  * At most 1008 problems and 65,280 block partial sums per call (a problem
  * uses min(512, ceil(M / 1024)) blocks); larger calls return SOS_E_INVALID.
- * A NaN or Inf shows up as a NaN loss.  The first call on a device looks up
+ * A NaN or Inf in c or p gives a non-finite loss (NaN or Inf); no status word
+ * reports it, so check the loss.  The first call on a device looks up
  * the array's device address (synchronously); make it before any stream
  * capture.  Every call shares the array, so calls that overlap on the GPU
  * (other streams, other threads) race; each call clears what must start at

@@ -24,7 +24,7 @@ SOS_VERDICT_ERROR, SOS_VERDICT_NOT_CONVERGED, SOS_VERDICT_SOS = -1, 0, 1
 PREC = {"bf16": SOS_BF16, "fp32": SOS_FP32, "fp64": SOS_FP64, "fp64_tc": SOS_FP64_TC}
 
 EXPORTS = [
-    "sos_plan_create", "sos_plan_destroy", "sos_plan_sizes", "sos_plan_monomials", "sos_plan_idx",
+    "sos_plan", "sos_plan_create", "sos_plan_destroy", "sos_plan_sizes", "sos_plan_monomials", "sos_plan_idx",
     "sos_workspace_size", "sos_workspace_init", "sos_coeffs", "sos_loss_grad",
     "sos_workspace_size_batched", "sos_loss_grad_batched", "sos_step", "sos_read_status",
     "sos_certify", "sos_diag_gemm_bf16", "sos_launch_count", "sos_timing_enable",
@@ -32,7 +32,7 @@ EXPORTS = [
     "sos_solve", "sos_group_create", "sos_group_destroy", "sos_group_scratch_size", "sos_group_set",
     "sos_group_clear", "sos_group_sync", "sos_group_run", "sos_group_losses", "sos_group_state",
     "sos_convert", "sos_group_set_lr", "sos_diag_bounded_wait", "sos_layer_workspace_size",
-    "sos_layer_expand", "sos_layer_loss_grad", "sos_layer_step", "sos_last_error",
+    "sos_layer_expand", "sos_layer_loss_grad", "sos_layer_step", "sos_last_error", "sos_plan_device_idx",
 ]
 
 
@@ -110,7 +110,9 @@ def lib(auto_build: bool = True):
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     P = ctypes.POINTER
     sig = {
+        "sos_plan": [i32, i32, i64, P(vp)],
         "sos_plan_create": [i32, i32, i64, P(vp)],
+        "sos_plan_device_idx": [vp, i64, i64, vp],
         "sos_plan_destroy": [vp],
         "sos_plan_sizes": [vp, P(i64), P(i64), P(i64)],
         "sos_plan_monomials": [vp, i32, vp],
@@ -171,6 +173,12 @@ def _check(rc: int) -> int:
 
 # ---- same-named wrappers ---------------------------------------------------------
 
+def sos_plan(n: int, two_d: int, r: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sos_plan(n, two_d, r, ctypes.byref(h)))
+    return h.value
+
+
 def sos_plan_create(n: int, two_d: int, r: int) -> int:
     h = ctypes.c_void_p()
     _check(lib().sos_plan_create(n, two_d, r, ctypes.byref(h)))
@@ -193,6 +201,10 @@ def sos_plan_monomials(plan: int, which: int, out_ptr: int) -> None:
 
 def sos_plan_idx(plan: int, out_ptr: int) -> None:
     _check(lib().sos_plan_idx(plan, out_ptr))
+
+
+def sos_plan_device_idx(plan: int, row0: int, rows: int, out_ptr: int) -> None:
+    _check(lib().sos_plan_device_idx(plan, row0, rows, out_ptr))
 
 
 def sos_workspace_size(plan: int, prec: int) -> int:

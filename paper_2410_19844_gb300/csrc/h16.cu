@@ -203,12 +203,13 @@ int make_idx_map(CUtensorMap* m, const int32_t* idx, int64_t N, int64_t ld) {
 }  // namespace
 
 int launch_build_h16(const sos_plan_s* p, const float* resid, void* h16, int32_t* status, cudaStream_t st) {
-    static int configured = 0;
-    if (!configured) {
+    int configured = 0;
+    SOS_CHECK(per_device_value((const void*)build_h16_tma_kernel, &configured, [](int* v) -> int {
         SOS_CUDA(cudaFuncSetAttribute(build_h16_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
-        configured = 1;
-    }
+        *v = 1;
+        return SOS_OK;
+    }));
     const int64_t T = ceil_div(p->N, TILE);
     if (T > 65535) return fail(SOS_E_UNSUPPORTED, "build_h16: too many tiles");
     CUtensorMap mi, mh;

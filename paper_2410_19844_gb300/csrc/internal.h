@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 #include <cstdint>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -55,6 +56,13 @@ class TraceRange {
     TraceRange(const TraceRange&) = delete;
     TraceRange& operator=(const TraceRange&) = delete;
 };
+
+// Kernel attributes (the dynamic shared-memory limit) and occupancy figures
+// belong to a device: a process-wide "done" flag would skip them on a second
+// GPU, and the first calls of two threads would race on it.  Runs
+// setup(value) once per (key, current device) under a lock and hands back
+// the value it produced on later calls.  Returns setup's status.
+int per_device_value(const void* key, int* value, const std::function<int(int*)>& setup);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }

@@ -33,7 +33,7 @@ constexpr int B_BYTES = BN * BK * 2;             // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 48 KB
 constexpr int BAR_BYTES = 256;
 constexpr int EPI_WARPS = 4;
-constexpr int EPI_STAGE_BYTES = EPI_WARPS * 32 * 33 * 4;   // transposition buffers
+constexpr int EPI_STAGE_BYTES = EPI_WARPS * STAGE_FLOATS * 4;   // transposition buffers
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EPI_STAGE_BYTES;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
@@ -185,14 +185,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             tc_fence_after();
             const int2 tile = tiles[t];
-            float* stage = epi_stage + (warp - 2) * 32 * STAGE_LD;
+            float* stage = epi_stage + (warp - 2) * STAGE_FLOATS;
 #pragma unroll 1
             for (int ch = 0; ch < BN / 32; ++ch) {
                 uint32_t v[32];
                 tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
                 tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) stage[lane * STAGE_LD + j] = __uint_as_float(v[j]);
+                for (int j = 0; j < 32; ++j) stage[stage_idx(lane, j)] = __uint_as_float(v[j]);
                 __syncwarp();
                 epi(tile.x * BM + q * 32, tile.y * BN + ch * 32, stage, lane);
                 __syncwarp();
@@ -252,12 +252,13 @@ namespace tc {
 template <bool B_MN, class Epi>
 static int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
                        int num_sms, const Epi& epi, int32_t* status, cudaStream_t st) {
-    static bool configured = false;
     auto kern = tc_gemm_kernel<B_MN, Epi>;
-    if (!configured) {
+    int configured = 0;
+    SOS_CHECK(per_device_value((const void*)kern, &configured, [kern](int* v) -> int {
         SOS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        configured = true;
-    }
+        *v = 1;
+        return SOS_OK;
+    }));
     if (num_tiles <= 0) return SOS_OK;
     const int grid = num_tiles < num_sms ? num_tiles : num_sms;
     {

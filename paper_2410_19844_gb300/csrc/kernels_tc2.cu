@@ -56,7 +56,7 @@ constexpr int A_BYTES = KATOMS * ATOM_A;          // per stage
 constexpr int B_BYTES = KATOMS * ATOM_B;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 64 KB per CTA
 constexpr int BAR_BYTES = 256;
-constexpr int EPI_STAGE_BYTES = 4 * 32 * 33 * 4;
+constexpr int EPI_STAGE_BYTES = 4 * STAGE_FLOATS * 4;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EPI_STAGE_BYTES;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
@@ -245,7 +245,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             }
             tc_fence_after();
             const int2 tile = tiles[t];
-            float* stage = epi_stage + (warp - 2) * 32 * STAGE_LD;
+            float* stage = epi_stage + (warp - 2) * STAGE_FLOATS;
             const int row0 = tile.x * PAIR_M + (int)rank * BM + q * 32;
             const int col0 = tile.y < 0 ? (-tile.y - 1) * (BN / 2) : tile.y * BN;
             const int nch = tile.y < 0 ? BN / 64 : BN / 32;
@@ -255,7 +255,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
                 tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) stage[lane * STAGE_LD + j] = __uint_as_float(v[j]);
+                for (int j = 0; j < 32; ++j) stage[stage_idx(lane, j)] = __uint_as_float(v[j]);
                 __syncwarp();
                 epi(row0, col0 + ch * 32, stage, lane);
                 __syncwarp();
@@ -321,13 +321,14 @@ template <bool B_MN, class Epi>
 int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
                      const Epi& epi, int32_t* status, cudaStream_t st) {
     using namespace tc2;
-    static int max_pairs = -1;
     auto kern = tc_gemm_pair_kernel<B_MN, Epi>;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     pair_launch_config(cfg, attr, st);
     // every pair resident at once: the tile loop assumes it
-    if (max_pairs < 0) SOS_CHECK(resident_pairs((const void*)kern, &max_pairs));
+    int max_pairs = 0;
+    SOS_CHECK(per_device_value((const void*)kern, &max_pairs,
+                               [kern](int* v) -> int { return resident_pairs((const void*)kern, v); }));
     if (num_tiles <= 0) return SOS_OK;
     const int pairs = num_tiles < max_pairs ? num_tiles : max_pairs;
     cfg.gridDim = dim3(2 * pairs);
@@ -341,10 +342,8 @@ int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, cons
 }  // namespace
 
 int adjoint_pair_capacity(int* pairs) {
-    static int cached = -1;
-    if (cached < 0) SOS_CHECK(resident_pairs((const void*)tc2::tc_gemm_pair_kernel<true, tc::UpdateEpilogue>, &cached));
-    *pairs = cached;
-    return SOS_OK;
+    const void* kern = (const void*)tc2::tc_gemm_pair_kernel<true, tc::UpdateEpilogue>;
+    return per_device_value(kern, pairs, [kern](int* v) -> int { return resident_pairs(kern, v); });
 }
 
 int launch_tc_forward_pair(const sos_plan_s* p, const void* a16, float* c, int32_t* status, cudaStream_t st) {

@@ -163,6 +163,8 @@ int sos_plan_create(int n, int two_d, int64_t r, sos_plan_t* out) {
     return SOS_OK;
 }
 
+int sos_plan(int n, int two_d, int64_t r, sos_plan_t* out) { return sos_plan_create(n, two_d, r, out); }
+
 int sos_plan_destroy(sos_plan_t p) {
     if (!p) return SOS_OK;
     if (p->dev.device >= 0) {
@@ -216,6 +218,17 @@ int sos_plan_idx(sos_plan_t p, int32_t* idx) {
             idx[a * N + b] = g;
         }
     }
+    return SOS_OK;
+}
+
+int sos_plan_device_idx(sos_plan_t p, int64_t row0, int64_t rows, int32_t* idx) {
+    if (!p || !idx || row0 < 0 || rows < 0 || row0 + rows > p->N)
+        return fail(SOS_E_INVALID, "sos_plan_device_idx: bad argument");
+    SOS_CHECK(ensure_device(p));
+    if (rows == 0) return SOS_OK;
+    const size_t row_bytes = (size_t)p->N * sizeof(int32_t);
+    SOS_CUDA(cudaMemcpy2D(idx, row_bytes, p->dev.idx + row0 * p->ld_idx, (size_t)p->ld_idx * sizeof(int32_t),
+                          row_bytes, (size_t)rows, cudaMemcpyDeviceToHost));
     return SOS_OK;
 }
 

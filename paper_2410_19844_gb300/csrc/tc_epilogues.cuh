@@ -22,12 +22,25 @@ namespace tc {
 //
 // The epilogue warps read the accumulator 32 x 32 at a time: warp q (= warp % 4)
 // owns rows 32q .. 32q+31 of the 128-row tile, and each tcgen05.ld gives lane i
-// row 32q+i, 32 consecutive columns.  The block is transposed through padded
-// shared memory (stage[i * 33 + j] = row i, column j) so that an epilogue works
-// with lane j = column j and walks the 32 rows: every global load and store of
-// a row segment is then one coalesced 128-byte access.
+// row 32q+i, 32 consecutive columns.  The block is transposed through shared
+// memory so that an epilogue works with lane j = column j and walks the 32
+// rows: every global load and store of a row segment is then one coalesced
+// 128-byte access.
+//
+// The 32 x 32 float block is stored unpadded, row i, column j at
+// stage_idx(i, j) = 32 i + (j XOR stage_swz(i)), where stage_swz moves the two
+// low bits of i to bits 3-4 and its three high bits to bits 0-2 (a permutation
+// of 0..31).  Each of the three access patterns then reaches 32 distinct banks:
+//   * the row write after tcgen05.ld (lane = row i, fixed column j): bank
+//     j ^ swz(i), distinct because swz is a permutation;
+//   * a row read (fixed row i, lane = column j): bank j ^ swz(i);
+//   * the forward's 4 x 8 patch read (lane = 8 dr + dc at row 4u + dr, column
+//     8v + dc): bits 0-2 of the bank are dc ^ u and bits 3-4 are v ^ dr.
 
-constexpr int STAGE_LD = 33;
+constexpr int STAGE_FLOATS = 32 * 32;
+
+__device__ __forceinline__ int stage_swz(int i) { return ((i & 3) << 3) | ((i >> 2) & 7); }
+__device__ __forceinline__ int stage_idx(int i, int j) { return i * 32 + (j ^ stage_swz(i)); }
 
 // Forward: c[idx(a, b)] += w G_ab for b >= a (w = 1 on the diagonal, 2 above).
 // The warp walks the 32 x 32 block in 4 x 8 patches (lane = 8 dr + dc: row
@@ -56,7 +69,7 @@ struct SegmentSumEpilogue {
         for (int t = 0; t < 32; ++t) {
             if (g[t] >= 0) {
                 const int i = 4 * (t >> 2) + dr, j = 8 * (t & 3) + dc;
-                const float v = stage[i * STAGE_LD + j];
+                const float v = stage[stage_idx(i, j)];
                 atomicAdd(c + g[t], a0 + i == b0 + j ? v : 2.0f * v);
             }
         }
@@ -105,7 +118,7 @@ struct SliceSumEpilogue {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (g[i] >= 0) {
-                const double v = (double)stage[i * STAGE_LD + lane] * pow2_int(ex[al + i] + eb);
+                const double v = (double)stage[stage_idx(i, lane)] * pow2_int(ex[al + i] + eb);
                 atomicAdd(c + g[i], (full || al + i != b) ? 2.0 * v : v);
             }
         }
@@ -158,7 +171,7 @@ struct SliceGroupEpilogue {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (gi[i] >= 0) {
-                const double v = (double)stage[i * STAGE_LD + lane] * pow2_int(ex[al + i] + eb);
+                const double v = (double)stage[stage_idx(i, lane)] * pow2_int(ex[al + i] + eb);
                 atomicAdd(c + gi[i], al + i != b ? 2.0 * v : v);
             }
         }
@@ -181,7 +194,7 @@ struct StoreEpilogue {
         for (int i = 0; i < 32; ++i) {
             const int a = a0 + i;
             if (a >= rows) break;
-            out[(int64_t)a * ld + k] = scale * stage[i * STAGE_LD + lane];
+            out[(int64_t)a * ld + k] = scale * stage[stage_idx(i, lane)];
         }
     }
 };
@@ -229,7 +242,7 @@ struct UpdateEpilogue {
             for (int i = 0; i < 16; ++i) {
                 if (h + i >= nrows) break;
                 const int64_t e = (int64_t)(a0 + h + i) * cols + k;
-                const float g = 2.0f * stage[(h + i) * STAGE_LD + lane];
+                const float g = 2.0f * stage[stage_idx(h + i, lane)];
                 float xi = x[i];
                 if (optimizer == SOS_GD) {
                     xi -= lr * g;

@@ -1,4 +1,5 @@
-// Launch counting and optional per-kernel CUDA-event timing.
+// Launch counting, optional per-kernel CUDA-event timing, and per-device
+// one-time kernel set-up.
 //
 // Every launcher in this library constructs a KernelScope.  It always counts
 // the launch; when timing is enabled it also records a CUDA event before and
@@ -40,7 +41,26 @@ cudaEvent_t take_event() {
     return e;
 }
 
+std::mutex g_dev_mu;
+std::map<std::pair<const void*, int>, int> g_dev_values;
+
 }  // namespace
+
+int per_device_value(const void* key, int* value, const std::function<int(int*)>& setup) {
+    int dev = -1;
+    SOS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    auto it = g_dev_values.find({key, dev});
+    if (it != g_dev_values.end()) {
+        *value = it->second;
+        return SOS_OK;
+    }
+    int v = 0;
+    SOS_CHECK(setup(&v));
+    g_dev_values[{key, dev}] = v;
+    *value = v;
+    return SOS_OK;
+}
 
 KernelScope::KernelScope(const char* name, cudaStream_t st) : name_(name), st_(st) {
     g_launches.fetch_add(1, std::memory_order_relaxed);

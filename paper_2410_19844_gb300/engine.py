@@ -33,7 +33,7 @@ class Plan:
         from math import comb
         N = comb(n + two_d // 2, two_d // 2)
         self.n, self.two_d = n, two_d
-        self.handle = L.sos_plan_create(n, two_d, int(r if r is not None else N))
+        self.handle = L.sos_plan(n, two_d, int(r if r is not None else N))
         self.N, self.M, self.r = L.sos_plan_sizes(self.handle)
         self._ws = {}
 
@@ -56,6 +56,13 @@ class Plan:
     def idx(self) -> np.ndarray:
         out = np.zeros((self.N, self.N), dtype=np.int32)
         L.sos_plan_idx(self.handle, out.ctypes.data)
+        return out
+
+    def device_idx(self, row0: int = 0, rows: int | None = None) -> np.ndarray:
+        """Rows of the index table the kernels read, copied back from the device."""
+        rows = self.N - row0 if rows is None else rows
+        out = np.zeros((rows, self.N), dtype=np.int32)
+        L.sos_plan_device_idx(self.handle, row0, rows, out.ctypes.data)
         return out
 
     # -- workspace ------------------------------------------------------------

@@ -27,6 +27,7 @@ import numpy as np
 import pytest
 import torch
 
+import bounds
 import oracle
 import sos_inputs
 from paper_2410_19844_gb300.engine import Optimizer, Plan
@@ -49,25 +50,8 @@ def full():
     return o, pl, A32, p32, coeffs, rows
 
 
-def _rows_ref(o, A, p, rows, u, u_r, gamma_c):
-    """Oracle rows of the gradient at A and their elementwise error bounds."""
-    absA = np.abs(A)
-    out = {}
-    for a in rows:
-        h = o.resid_row(A, p, a)
-        absc = o.resid_row(absA, np.zeros_like(p), a)          # |c| at the monomials a + b
-        dc = gamma_c * absc
-        dh = dc + u_r * (np.abs(h) + dc)
-        g = 2.0 * (h @ A)
-        bound = 2.0 * (dh @ absA) + 2.0 * o.N * u * ((np.abs(h) + dh) @ absA) + 1e-30
-        out[a] = (g, bound)
-    return out
-
-
-def _coeffs_ref(o, A, idx):
-    absA = np.abs(A)
-    return (np.array([o.coeff_at(A, int(g)) for g in idx]),
-            np.array([o.coeff_at(absA, int(g)) for g in idx]))
+_rows_ref = bounds.rows_ref
+_coeffs_ref = bounds.coeffs_ref
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])

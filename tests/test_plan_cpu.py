@@ -51,6 +51,17 @@ def test_invalid_plans_rejected(args):
     assert e.value.code == L.SOS_E_INVALID
 
 
+def test_sos_plan_is_plan_create_under_its_short_name():
+    h = L.sos_plan(20, 8, 10626)
+    try:
+        assert L.sos_plan_sizes(h) == (10626, 3108105, 10626)
+    finally:
+        L.sos_plan_destroy(h)
+    with pytest.raises(L.SOSError) as e:
+        L.sos_plan(3, 3, 1)
+    assert e.value.code == L.SOS_E_INVALID
+
+
 def test_too_many_coefficients_rejected():
     with pytest.raises(L.SOSError) as e:
         L.sos_plan_create(60, 12, 1)     # C(72, 12) > 2^31
@@ -93,3 +104,5 @@ def test_host_calls_validate_arguments():
         L.sos_plan_monomials(pl.handle, 2, 0)
     with pytest.raises(L.SOSError):
         L.sos_loss_grad(pl.handle, L.SOS_FP32, 0, 0, 0, 0, 0, 0)   # NULL A: rejected on the host
+    with pytest.raises(L.SOSError):
+        L.sos_plan_device_idx(pl.handle, 8, 5, 0)                 # rows beyond N: rejected on the host
