@@ -93,6 +93,9 @@ int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad
     if (prec == SOS_FP32)
         return launch_simt_adjoint<float>(p, static_cast<const float*>(A), resid, static_cast<float*>(grad), 1,
                                           st);
+    if (use_h_ring())
+        return launch_tc_adjoint_ring_pair(p, resid, at<char>(ws, w.ring), at<uint32_t>(ws, w.ring_flags),
+                                           at<char>(ws, w.a16), static_cast<float*>(grad), status, st);
     void* h16 = at<char>(ws, w.h16);
     SOS_CHECK(launch_build_h16(p, resid, h16, status, st));
     return use_cta_pairs()
@@ -233,11 +236,19 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         double* L = loss ? static_cast<double*>(loss) : at<double>(ws, w.loss);
         SOS_CHECK(launch_residual<float>(p, c, static_cast<const float*>(pv), resid, L, at<double>(ws, w.partials),
                                          status, 1, st));
-        void* h16 = at<char>(ws, w.h16);
-        SOS_CHECK(launch_build_h16(p, resid, h16, status, st));
-        auto adj = use_cta_pairs() ? launch_tc_adjoint_update_pair : launch_tc_adjoint_update;
-        SOS_CHECK(adj(p, h16, a16_cur, a16_next, static_cast<float*>(s->A), static_cast<float*>(s->m),
-                      static_cast<float*>(s->v), o->optimizer, t, o->lr, o->beta1, o->beta2, o->eps, status, st));
+        if (use_h_ring()) {
+            SOS_CHECK(launch_tc_adjoint_update_ring_pair(
+                p, resid, at<char>(ws, w.ring), at<uint32_t>(ws, w.ring_flags), a16_cur, a16_next,
+                static_cast<float*>(s->A), static_cast<float*>(s->m), static_cast<float*>(s->v), o->optimizer, t,
+                o->lr, o->beta1, o->beta2, o->eps, status, st));
+        } else {
+            void* h16 = at<char>(ws, w.h16);
+            SOS_CHECK(launch_build_h16(p, resid, h16, status, st));
+            auto adj = use_cta_pairs() ? launch_tc_adjoint_update_pair : launch_tc_adjoint_update;
+            SOS_CHECK(adj(p, h16, a16_cur, a16_next, static_cast<float*>(s->A), static_cast<float*>(s->m),
+                          static_cast<float*>(s->v), o->optimizer, t, o->lr, o->beta1, o->beta2, o->eps, status,
+                          st));
+        }
         s->flags = SOS_STATE_BF16_CURRENT | (cur ? 0 : SOS_STATE_BF16_INDEX);
         s->t = t;
         return SOS_OK;

@@ -21,9 +21,11 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 
+#include "h_ring.cuh"
 #include "internal.h"
 #include "tc_epilogues.cuh"
 #include "tc_ptx.cuh"
@@ -200,7 +202,39 @@ int make_idx_map(CUtensorMap* m, const int32_t* idx, int64_t N, int64_t ld) {
     return SOS_OK;
 }
 
+// First band of the H ring, and the ring's flags zeroed (h_ring.cuh): a grid
+// of 8-warp blocks walks the 64 x 64 units of panels 0 .. first_panel - 1,
+// each warp 8 rows of a unit.
+__global__ void __launch_bounds__(256) ring_prologue_kernel(RingArgs g, int flag_words) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < flag_words; i += stride) g.flags[i] = 0u;
+    const int units = g.units_per_panel();
+    const int64_t total = (int64_t)g.first_panel * units;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const int P = (int)(t / units);
+        ring_build_rows<8>(g, P, (int)(t - (int64_t)P * units), 8 * warp, lane);
+    }
+}
+
 }  // namespace
+
+namespace tc {
+
+int launch_ring_prologue(const RingArgs& g, int num_sms, cudaStream_t st) {
+    const int flag_words = kRingFlagsHeader + 2 * g.num_panels;
+    const int64_t total = (int64_t)g.first_panel * g.units_per_panel();
+    const int64_t want = std::max<int64_t>(total, 1);
+    const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms * 8);
+    {
+        KernelScope ks_("ring_prologue", st);
+        ring_prologue_kernel<<<grid, 256, 0, st>>>(g, flag_words);
+    }
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+}  // namespace tc
 
 int launch_build_h16(const sos_plan_s* p, const float* resid, void* h16, int32_t* status, cudaStream_t st) {
     int configured = 0;

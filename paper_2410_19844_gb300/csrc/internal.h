@@ -79,7 +79,9 @@ struct Workspace {
     size_t resid = 0;      // M residuals (float or double)
     size_t grad = 0;       // N x r gradient (float or double)
     size_t a16 = 0;        // 2 x N x ld16 bf16 copies of A, ping-pong (SOS_BF16 only)
-    size_t h16 = 0;        // N x ld16h bf16 H(resid)   (SOS_BF16 only)
+    size_t h16 = 0;        // N x ld16h bf16 H(resid)   (SOS_BF16 without the ring, SOS_FP64_TC)
+    size_t ring = 0;       // S x 256 x ld16h bf16 panels of H(resid) (SOS_BF16 with the ring)
+    size_t ring_flags = 0; // abort word, built and consumed counters of the ring
     size_t resid32 = 0;    // M float residuals         (SOS_FP64_TC only)
     size_t slices = 0;     // kMaxSlices x NP x ld16 bf16 slices of A, NP = N rounded up to 256 (SOS_FP64_TC)
     size_t ex = 0;         // N int32 row exponents     (SOS_FP64_TC only)
@@ -110,6 +112,7 @@ struct DeviceTables {
     int num_adj_tiles = 0;
     int2* fwd_tiles2 = nullptr;  // the same in 256 x 256 tiles, for CTA pairs
     int2* adj_tiles2 = nullptr;  // entries with y < 0: narrow tiles, 128 columns from 128 (-y - 1)
+    int32_t* panel_tiles = nullptr;  // per 256-row block: the adjoint tiles (of adj_tiles2) that read it
     int num_fwd_tiles2 = 0;
     int num_adj_tiles2 = 0;
     // pair lists of the Gram identity, grouped by coefficient (built on demand):
@@ -153,6 +156,22 @@ struct sos_plan_s {
 namespace sos {
 
 Workspace workspace_layout(const sos_plan_s* plan, int prec);
+
+// Whether the BF16 adjoint reads H(r) from band-local panels that the kernel
+// builds itself instead of a materialised H (environment variable SOS_H_RING
+// = 1, read once; only with the CTA-pair kernels).  Off by default: measured
+// on the large workload it is about 9% slower than materialising H, and it
+// holds a few bands of panels instead of the whole N x N H.
+bool use_h_ring();
+// Row-block band height of the adjoint's tile list (SOS_BAND_ADJ, default 8).
+int adjoint_band();
+// The ring of H panels: G = band height, S = slots (D G for a depth of D bands,
+// SOS_RING_DEPTH, default 3; at most the number of 256-row panels), panels =
+// ceil(N / 256).
+struct RingGeometry {
+    int band, slots, panels;
+};
+RingGeometry ring_geometry(const sos_plan_s* plan);
 int ensure_device(sos_plan_s* plan);
 int ensure_pair_lists(sos_plan_s* plan);
 
@@ -197,6 +216,15 @@ int launch_tc_adjoint_update(const sos_plan_s* plan, const void* h16, const void
 int launch_tc_forward_pair(const sos_plan_s* plan, const void* a16, float* c, int32_t* status, cudaStream_t st);
 int launch_tc_adjoint_pair(const sos_plan_s* plan, const void* h16, const void* a16, float* grad,
                            int32_t* status, cudaStream_t st);
+// The same two adjoints reading H(resid) from the ring in the workspace
+// (`ring`, `flags`): a prologue kernel builds the first band of panels and
+// zeroes the flags, the adjoint's builder warps build the rest.
+int launch_tc_adjoint_ring_pair(const sos_plan_s* plan, const float* resid, void* ring, uint32_t* flags,
+                                const void* a16, float* grad, int32_t* status, cudaStream_t st);
+int launch_tc_adjoint_update_ring_pair(const sos_plan_s* plan, const float* resid, void* ring, uint32_t* flags,
+                                       const void* a16_cur, void* a16_next, float* A, float* m, float* v,
+                                       int optimizer, int64_t t, double lr, double b1, double b2, double eps,
+                                       int32_t* status, cudaStream_t st);
 int launch_tc_adjoint_update_pair(const sos_plan_s* plan, const void* h16, const void* a16_cur, void* a16_next,
                                   float* A, float* m, float* v, int optimizer, int64_t t, double lr, double b1,
                                   double b2, double eps, int32_t* status, cudaStream_t st);

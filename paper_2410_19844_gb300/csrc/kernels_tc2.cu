@@ -17,6 +17,11 @@
 // the status word and unwinds, and both CTAs still meet at the final cluster
 // barrier before TMEM is released.
 //
+// With RING (the BF16 adjoint), the A operand is H(r) read from band-local
+// panels in a ring instead of a materialised H, and two more warps build the
+// panels while the MMAs run (h_ring.cuh):
+//   warps 6-7 (both CTAs)        : builders of the CTA's share of later panels
+//
 // A tile entry (x, y) is row block x of 256 and column block y of 256.  An
 // entry with y < 0 is a narrow tile: columns 128 (-y - 1) onwards, 128 wide,
 // computed with N = 128 MMAs (each CTA supplies 64 columns of B).  The tile
@@ -29,6 +34,7 @@
 
 #include <cmath>
 
+#include "h_ring.cuh"
 #include "internal.h"
 #include "tc_epilogues.cuh"
 #include "tc_ptx.cuh"
@@ -59,14 +65,20 @@ constexpr int BAR_BYTES = 256;
 constexpr int EPI_STAGE_BYTES = 4 * STAGE_FLOATS * 4;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EPI_STAGE_BYTES;
 constexpr int THREADS = 192;
+constexpr int RING_BUILDER_WARPS = 2;
+constexpr int RING_THREADS = THREADS + 32 * RING_BUILDER_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
-template <bool B_MN_MAJOR, class Epilogue>
-__global__ void __launch_bounds__(THREADS, 1)
+__host__ __device__ constexpr int threads_of(bool ring) { return ring ? RING_THREADS : THREADS; }
+
+template <bool B_MN_MAJOR, class Epilogue, bool RING = false>
+__global__ void __launch_bounds__(threads_of(RING), 1)
 tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int nkb,
-                    const int2* __restrict__ tiles, int num_tiles, Epilogue epi, int32_t* __restrict__ status) {
+                    const int2* __restrict__ tiles, int num_tiles, Epilogue epi, int32_t* __restrict__ status,
+                    RingArgs ring) {
     static_assert(!(Epilogue::kSegmented && B_MN_MAJOR), "segmented K runs with K-major operands only");
+    static_assert(!(Epilogue::kSegmented && RING), "the H ring serves the adjoint only");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* base = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -79,6 +91,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
     uint64_t* drain = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile uint32_t* err = tmem_slot + 1;
+    volatile uint32_t* bstop = tmem_slot + 2;     // the ring builders' common decision to stop
     float* epi_stage = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + BAR_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -97,6 +110,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
         }
         mbar_init(drain, 1);
         *err = 0;
+        *bstop = 0;
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -119,7 +133,18 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
         for (int t = pair; t < num_tiles && ok; t += num_pairs) {
             const int2 tile = tiles[t];
             const bool narrow = tile.y < 0;
-            const int arow = tile.x * PAIR_M + (int)rank * BM;
+            int arow = tile.x * PAIR_M + (int)rank * BM;
+            if constexpr (RING) {
+                // the tile's rows of H are panel tile.x, in its ring slot
+                if (tile.x >= ring.first_panel) {
+                    if (!wait_counter(ring.built(tile.x), gridDim.x, ring.abort_word(), WAIT_LIMIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async_global();
+                }
+                arow = (tile.x % ring.S) * PAIR_M + (int)rank * BM;
+            }
             const int bcol = narrow ? (-tile.y - 1) * (BN / 2) + (int)rank * (BN / 4)
                                     : tile.y * BN + (int)rank * (BN / 2);
             int nkbt = nkb;       // K blocks of this tile (all its segments)
@@ -164,6 +189,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
         if (!ok) {
             *err = 1;
             atomicCAS(status, 0, SOS_E_TIMEOUT);
+            if constexpr (RING) atomicExch(ring.abort_word(), 1u);
         }
         // The leader's full barriers count both CTAs' copies: let them land.
         if (leader)
@@ -224,10 +250,11 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
         if (!ok) {
             *err = 1;
             atomicCAS(status, 0, SOS_E_TIMEOUT);
+            if constexpr (RING) atomicExch(ring.abort_word(), 1u);
         }
         umma_commit_pair_multicast(drain, 0x1);
         mbar_wait(drain, 0, WAIT_LIMIT_NS);
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < 6) {
         // ---------------- epilogue (both CTAs) ----------------
         const int q = warp & 3;
         const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), 0);
@@ -240,11 +267,16 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 if (lane == 0) {
                     *err = 1;
                     atomicCAS(status, 0, SOS_E_TIMEOUT);
+                    if constexpr (RING) atomicExch(ring.abort_word(), 1u);
                 }
                 break;
             }
             tc_fence_after();
             const int2 tile = tiles[t];
+            if constexpr (RING) {
+                // the tile's MMAs are done, so both CTAs' loads of its panel have landed
+                if (leader && warp == 2 && lane == 0) red_release_gpu_add(ring.consumed(tile.x), 1u);
+            }
             float* stage = epi_stage + (warp - 2) * STAGE_FLOATS;
             const int row0 = tile.x * PAIR_M + (int)rank * BM + q * 32;
             const int col0 = tile.y < 0 ? (-tile.y - 1) * (BN / 2) : tile.y * BN;
@@ -263,6 +295,53 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(tempty_leader0 + (uint32_t)(buf * sizeof(uint64_t)));
+        }
+    }
+    if constexpr (RING) {
+        if (warp >= 6) {
+            // ---------------- panel builders (both CTAs) ----------------
+            const int w = warp - 6, bt = threadIdx.x - THREADS;
+            const int units = ring.units_per_panel();
+            const int cta = (int)blockIdx.x, nctas = (int)gridDim.x;
+            bool ok = true;
+            // the index rows of the next panel go to L2 while this one is built,
+            // so the builders' loads hit L2 instead of waiting on DRAM
+            if (ring.first_panel < ring.num_panels)
+                for (int u = cta; u < units; u += nctas) ring_prefetch_unit(ring, ring.first_panel, u, bt, 32 * RING_BUILDER_WARPS);
+            for (int P = ring.first_panel; P < ring.num_panels && ok; ++P) {
+                if (P + 1 < ring.num_panels)
+                    for (int u = cta; u < units; u += nctas) ring_prefetch_unit(ring, P + 1, u, bt, 32 * RING_BUILDER_WARPS);
+                if (P >= ring.S) {
+                    // Slot P mod S is free once every tile of panel P - S is done with
+                    // it.  One thread waits and writes the builders' common decision
+                    // before the barrier; every builder reads it after the barrier, so
+                    // all of them leave together or none does (the next write comes
+                    // only after the barrier that ends this panel).
+                    if (threadIdx.x == THREADS) {
+                        bool freed = wait_counter(ring.consumed(P - ring.S), (uint32_t)ring.panel_tiles[P - ring.S],
+                                                  ring.abort_word(), WAIT_LIMIT_NS);
+                        *bstop = (!freed || *err) ? 1u : 0u;
+                    }
+                    named_bar_sync(1, 32 * RING_BUILDER_WARPS);
+                    if (*bstop) {
+                        ok = false;
+                        break;
+                    }
+                }
+                for (int u = cta; u < units; u += nctas)
+                    for (int r0 = 32 * w; r0 < 64; r0 += 32 * RING_BUILDER_WARPS)
+                        ring_build_rows<32>(ring, P, u, r0, lane);
+                fence_proxy_async_global();
+                named_bar_sync(1, 32 * RING_BUILDER_WARPS);
+                if (threadIdx.x == THREADS) {
+                    __threadfence();
+                    red_release_gpu_add(ring.built(P), 1u);
+                }
+            }
+            if (!ok && threadIdx.x == THREADS) {
+                atomicCAS(status, 0, SOS_E_TIMEOUT);
+                atomicExch(ring.abort_word(), 1u);
+            }
         }
     }
     if (*err) {
@@ -285,30 +364,36 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
 
 namespace {
 
-void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cudaStream_t st) {
+// Clusters of two CTAs; with `cooperative` the launch also guarantees that
+// every CTA of the grid is resident at once (the H ring's builders and
+// producers wait on one another across CTAs).
+void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cudaStream_t st, int threads,
+                        bool cooperative) {
     using namespace tc2;
     cfg = {};
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(THREADS);
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = cooperative ? 2 : 1;
 }
 
 // How many CTA pairs of `kern` fit on the current GPU at once.
-int resident_pairs(const void* kern, int* out) {
+int resident_pairs(const void* kern, int threads, int* out) {
     using namespace tc2;
     SOS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     int dev = 0, sms = 0;
     SOS_CUDA(cudaGetDevice(&dev));
     SOS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute attr[1];
-    pair_launch_config(cfg, attr, 0);
+    cudaLaunchAttribute attr[2];
+    pair_launch_config(cfg, attr, 0, threads, false);
     cfg.gridDim = dim3(sms);
     int clusters = 0;
     SOS_CUDA(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
@@ -317,24 +402,29 @@ int resident_pairs(const void* kern, int* out) {
     return SOS_OK;
 }
 
-template <bool B_MN, class Epi>
+template <bool B_MN, class Epi, bool RING = false>
 int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
-                     const Epi& epi, int32_t* status, cudaStream_t st) {
+                     const Epi& epi, int32_t* status, cudaStream_t st, const tc::RingArgs& ring = tc::RingArgs{}) {
     using namespace tc2;
-    auto kern = tc_gemm_pair_kernel<B_MN, Epi>;
+    auto kern = tc_gemm_pair_kernel<B_MN, Epi, RING>;
+    const int threads = threads_of(RING);
     cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute attr[1];
-    pair_launch_config(cfg, attr, st);
+    cudaLaunchAttribute attr[2];
+    pair_launch_config(cfg, attr, st, threads, RING);
     // every pair resident at once: the tile loop assumes it
     int max_pairs = 0;
     SOS_CHECK(per_device_value((const void*)kern, &max_pairs,
-                               [kern](int* v) -> int { return resident_pairs((const void*)kern, v); }));
+                               [kern, threads](int* v) -> int { return resident_pairs((const void*)kern, threads, v); }));
     if (num_tiles <= 0) return SOS_OK;
-    const int pairs = num_tiles < max_pairs ? num_tiles : max_pairs;
+    // the ring's producers wait for every CTA's builders: the whole persistent
+    // grid runs even when there are fewer tiles than pairs
+    const int pairs = RING ? max_pairs : (num_tiles < max_pairs ? num_tiles : max_pairs);
     cfg.gridDim = dim3(2 * pairs);
+    const char* name = Epi::kName;
+    if constexpr (RING) name = Epi::kRingName;
     {
-        KernelScope ks_(Epi::kName, st);
-        SOS_CUDA(cudaLaunchKernelEx(&cfg, kern, mA, mB, nkb, tiles, num_tiles, epi, status));
+        KernelScope ks_(name, st);
+        SOS_CUDA(cudaLaunchKernelEx(&cfg, kern, mA, mB, nkb, tiles, num_tiles, epi, status, ring));
     }
     return SOS_OK;
 }
@@ -342,8 +432,12 @@ int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, cons
 }  // namespace
 
 int adjoint_pair_capacity(int* pairs) {
-    const void* kern = (const void*)tc2::tc_gemm_pair_kernel<true, tc::UpdateEpilogue>;
-    return per_device_value(kern, pairs, [kern](int* v) -> int { return resident_pairs(kern, v); });
+    // the tile lists are cut for the grid of the adjoint that sos_step runs
+    const bool ring = use_h_ring();
+    const void* kern = ring ? (const void*)tc2::tc_gemm_pair_kernel<true, tc::UpdateEpilogue, true>
+                            : (const void*)tc2::tc_gemm_pair_kernel<true, tc::UpdateEpilogue, false>;
+    const int threads = tc2::threads_of(ring);
+    return per_device_value(kern, pairs, [kern, threads](int* v) -> int { return resident_pairs(kern, threads, v); });
 }
 
 int launch_tc_forward_pair(const sos_plan_s* p, const void* a16, float* c, int32_t* status, cudaStream_t st) {
@@ -380,6 +474,69 @@ int launch_tc_adjoint_update_pair(const sos_plan_s* p, const void* h16, const vo
     epi.ld16 = p->ld16;
     return launch_pair_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles2, p->dev.num_adj_tiles2, epi,
                                   status, st);
+}
+
+namespace {
+
+tc::RingArgs ring_args(const sos_plan_s* p, const float* resid, void* ring, uint32_t* flags) {
+    const RingGeometry g = ring_geometry(p);
+    tc::RingArgs a;
+    a.idx = p->dev.idx;
+    a.ld_idx = p->ld_idx;
+    a.resid = resid;
+    a.ring = static_cast<__nv_bfloat16*>(ring);
+    a.ldh = p->ld16h;
+    a.N = (int)p->N;
+    a.S = g.slots;
+    a.first_panel = g.band;
+    a.num_panels = g.panels;
+    a.panel_tiles = p->dev.panel_tiles;
+    a.flags = flags;
+    return a;
+}
+
+}  // namespace
+
+int launch_tc_adjoint_update_ring_pair(const sos_plan_s* p, const float* resid, void* ring, uint32_t* flags,
+                                       const void* a16_cur, void* a16_next, float* A, float* m, float* v,
+                                       int optimizer, int64_t t, double lr, double b1, double b2, double eps,
+                                       int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    const tc::RingArgs ra = ring_args(p, resid, ring, flags);
+    SOS_CHECK(tc::launch_ring_prologue(ra, p->dev.num_sms, st));
+    CUtensorMap mH, mA;
+    SOS_CHECK(make_bf16_map(&mH, ring, p->N, (uint64_t)ra.S * PAIR_M, p->ld16h, BK, BM));
+    SOS_CHECK(make_bf16_map(&mA, a16_cur, p->r, p->N, p->ld16, 64, BK));
+    tc::UpdateEpilogue epi;
+    epi.rows = (int)p->N;
+    epi.cols = (int)p->r;
+    epi.optimizer = optimizer;
+    epi.lr = (float)lr;
+    epi.b1 = (float)b1;
+    epi.b2 = (float)b2;
+    epi.eps = (float)eps;
+    epi.c1 = (float)(1.0 - std::pow(b1, (double)t));
+    epi.c2 = (float)(1.0 - std::pow(b2, (double)t));
+    epi.A = A;
+    epi.m = m;
+    epi.v = v;
+    epi.a16_next = static_cast<__nv_bfloat16*>(a16_next);
+    epi.ld16 = p->ld16;
+    return launch_pair_gemm<true, tc::UpdateEpilogue, true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles2,
+                                                            p->dev.num_adj_tiles2, epi, status, st, ra);
+}
+
+int launch_tc_adjoint_ring_pair(const sos_plan_s* p, const float* resid, void* ring, uint32_t* flags,
+                                const void* a16, float* grad, int32_t* status, cudaStream_t st) {
+    using namespace tc2;
+    const tc::RingArgs ra = ring_args(p, resid, ring, flags);
+    SOS_CHECK(tc::launch_ring_prologue(ra, p->dev.num_sms, st));
+    CUtensorMap mH, mA;
+    SOS_CHECK(make_bf16_map(&mH, ring, p->N, (uint64_t)ra.S * PAIR_M, p->ld16h, BK, BM));
+    SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, 64, BK));
+    tc::StoreEpilogue epi{(int)p->N, (int)p->r, p->r, 2.0f, grad};
+    return launch_pair_gemm<true, tc::StoreEpilogue, true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles2,
+                                                           p->dev.num_adj_tiles2, epi, status, st, ra);
 }
 
 int launch_tc_adjoint_pair(const sos_plan_s* p, const void* h16, const void* a16, float* grad, int32_t* status,

@@ -86,7 +86,13 @@ Workspace workspace_layout(const sos_plan_s* p, int prec) {
     w.grad = take((size_t)p->N * (size_t)p->r * (prec == SOS_FP64_TC ? 4 : elt));
     if (prec == SOS_BF16) {
         w.a16 = take(2 * (size_t)p->N * (size_t)p->ld16 * 2);
-        w.h16 = take((size_t)p->N * (size_t)p->ld16h * 2);
+        if (use_h_ring()) {
+            const RingGeometry g = ring_geometry(p);
+            w.ring = take((size_t)g.slots * 256 * (size_t)p->ld16h * 2);
+            w.ring_flags = take(((size_t)64 + 2 * (size_t)g.panels) * sizeof(uint32_t));
+        } else {
+            w.h16 = take((size_t)p->N * (size_t)p->ld16h * 2);
+        }
     }
     if (prec == SOS_FP64_TC) {
         w.a16 = take((size_t)p->N * (size_t)p->ld16 * 2);
@@ -176,6 +182,7 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.adj_tiles);
         cudaFree(p->dev.fwd_tiles2);
         cudaFree(p->dev.adj_tiles2);
+        cudaFree(p->dev.panel_tiles);
         cudaFree(p->dev.pair_ptr);
         cudaFree(p->dev.pair_pos);
         cudaFree(p->dev.form_rows);
@@ -274,7 +281,7 @@ static void make_tiles(const sos_plan_s* p, int pairs, std::vector<int2>& fwd, s
         const int v = e ? std::atoi(e) : 0;
         return v > 0 ? v : dflt;
     };
-    const int bf = env_band("SOS_BAND_FWD", 8), ba = env_band("SOS_BAND_ADJ", 8);
+    const int bf = env_band("SOS_BAND_FWD", 8), ba = adjoint_band();
     for (int i0 = 0; i0 < TP; i0 += bf) {
         const int i1 = std::min(TP, i0 + bf);
         for (int J = i0; J < TP; ++J)
@@ -305,6 +312,42 @@ static void make_tiles(const sos_plan_s* p, int pairs, std::vector<int2>& fwd, s
     }
 }
 
+int adjoint_band() {
+    static const int v = [] {
+        const char* e = std::getenv("SOS_BAND_ADJ");
+        const int b = e ? std::atoi(e) : 0;
+        return b > 0 ? b : 8;
+    }();
+    return v;
+}
+
+bool use_h_ring() {
+    static const bool v = [] {
+        const char* e = std::getenv("SOS_H_RING");
+        return e && e[0] == '1';
+    }();
+    return v && use_cta_pairs();
+}
+
+// Slots of the ring in bands (SOS_RING_DEPTH, default 3, at least 2): with
+// depth D, the builders of band b + D - 1 need only band b - 1 to be done.
+static int ring_depth() {
+    static const int v = [] {
+        const char* e = std::getenv("SOS_RING_DEPTH");
+        const int d = e ? std::atoi(e) : 0;
+        return d >= 2 ? d : 3;
+    }();
+    return v;
+}
+
+RingGeometry ring_geometry(const sos_plan_s* p) {
+    RingGeometry g;
+    g.panels = (int)ceil_div(p->N, 256);
+    g.band = std::min(adjoint_band(), g.panels);
+    g.slots = std::min(ring_depth() * g.band, g.panels);
+    return g;
+}
+
 bool use_cta_pairs() {
     static int v = -1;
     if (v < 0) {
@@ -329,9 +372,16 @@ int ensure_device(sos_plan_s* p) {
     int pairs = 0;
     if (use_cta_pairs()) SOS_CHECK(adjoint_pair_capacity(&pairs));
     make_tiles(p, pairs, fwd, adj, fwd2, adj2);
+    // adjoint tiles per 256-row panel (the ring's slot-release counts)
+    std::vector<int32_t> panel_tiles((size_t)ceil_div(p->N, 256), 0);
+    for (const int2& tl : adj2) panel_tiles[tl.x]++;
     uint8_t* d_S = nullptr;
     int32_t* d_phi = nullptr;
     cudaError_t e = cudaMalloc(&t.idx, idx_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&t.panel_tiles, panel_tiles.size() * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.panel_tiles, panel_tiles.data(), panel_tiles.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&t.fwd_tiles, fwd.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&t.adj_tiles, adj.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&t.fwd_tiles2, fwd2.size() * sizeof(int2));
@@ -367,6 +417,7 @@ int ensure_device(sos_plan_s* p) {
         cudaFree(t.adj_tiles);
         cudaFree(t.fwd_tiles2);
         cudaFree(t.adj_tiles2);
+        cudaFree(t.panel_tiles);
         return rc;
     }
     t.num_fwd_tiles = (int)fwd.size();

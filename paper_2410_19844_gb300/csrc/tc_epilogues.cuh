@@ -181,6 +181,7 @@ struct SliceGroupEpilogue {
 // Adjoint / diagnostic GEMM: out[row][col] = scale * acc.
 struct StoreEpilogue {
     static constexpr const char* kName = "tc_adjoint";
+    static constexpr const char* kRingName = "tc_adjoint_ring";
     static constexpr bool kSegmented = false;
     int rows, cols;
     int64_t ld;
@@ -209,6 +210,7 @@ struct DiagEpilogue : StoreEpilogue {
 // is still being read as an operand by other tiles).
 struct UpdateEpilogue {
     static constexpr const char* kName = "tc_adjoint_update";
+    static constexpr const char* kRingName = "tc_adjoint_update_ring";
     static constexpr bool kSegmented = false;
     int rows, cols, optimizer;
     float lr, b1, b2, eps, c1, c2;

@@ -234,5 +234,45 @@ __device__ __forceinline__ void umma_commit_pair_multicast(uint64_t* bar, uint16
         : "memory");
 }
 
+// ---- flags between CTAs of one grid (global memory) -----------------------------
+
+// Load with acquire semantics at GPU scope: later reads of this thread see
+// every write that the releasing thread made before its release.
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Atomic add with release semantics at GPU scope.
+__device__ __forceinline__ void red_release_gpu_add(uint32_t* p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Orders this thread's global-memory accesses through the generic proxy
+// (ordinary loads and stores) with those through the async proxy (TMA).
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Named barrier `id` over `count` threads (a multiple of 32) of the CTA.
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Waits until *ctr >= target, polling with a short sleep.  Gives up (false)
+// when *abort becomes non-zero or after limit_ns; the caller records the
+// failure and unwinds.
+__device__ __forceinline__ bool wait_counter(const uint32_t* ctr, uint32_t target, const volatile uint32_t* abort,
+                                             uint64_t limit_ns) {
+    if (ld_acquire_gpu(ctr) >= target) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        __nanosleep(64);
+        if (ld_acquire_gpu(ctr) >= target) return true;
+        if (*abort != 0u || global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
 }  // namespace tc
 }  // namespace sos

@@ -67,12 +67,12 @@ def test_multiblock_problem_matches():
     """M large enough that each problem is reduced by several blocks, whose
     ticket counters must start from zero on every call."""
     pl = Plan(10, 10, r=64)             # M = 184,756: 181 blocks per problem
-    o_res = oracle.Oracle(1, 2).residual   # residual() needs no tables of this plan's size
+    o = oracle.Oracle(10, 10)
     A = torch.from_numpy(sos_inputs.normal_matrix(pl.N, pl.r, seed=3, sigma=0.2)).float().cuda()
     p = torch.from_numpy(sos_inputs.normal_matrix(pl.M, 1, seed=4)[:, 0]).float().cuda()
     want_loss, _, _ = pl.loss_grad(A, p, "fp32", want_grad=False)
     c = pl.coeffs(A, "fp32")
-    loss_ref, _ = o_res(c.double().cpu().numpy(), p.double().cpu().numpy())
+    loss_ref, _ = o.residual(c.double().cpu().numpy(), p.double().cpu().numpy())
     for _ in range(2):
         loss = torch.zeros(2, dtype=torch.float64, device="cuda")
         L.sos_loss_from_coeffs_static(L.SOS_FP32, 1, pl.M, c.data_ptr(), p.data_ptr(), 0, loss.data_ptr(),
