@@ -59,8 +59,13 @@ int forward(sos_plan_s* p, int prec, const void* A, void* ws, cudaStream_t st, v
     if (prec == SOS_FP32) return launch_simt_forward<float, float>(p, static_cast<const float*>(A), c, 1, st);
     void* a16 = at<char>(ws, w.a16);
     SOS_CHECK(launch_cast_bf16(static_cast<const float*>(A), p->N, p->r, a16, p->ld16, st));
-    return use_cta_pairs() ? launch_tc_forward_pair(p, a16, c, at<int32_t>(ws, w.status), st)
-                           : launch_tc_forward(p, a16, c, at<int32_t>(ws, w.status), st);
+    if (!use_cta_pairs()) return launch_tc_forward(p, a16, c, at<int32_t>(ws, w.status), st);
+    float* diag = nullptr;
+    if (use_exact_diag()) {
+        diag = at<float>(ws, w.diag);
+        SOS_CHECK(launch_diag_sumsq(a16, p->ld16, p->N, p->r, diag, st));
+    }
+    return launch_tc_forward_pair(p, a16, c, at<int32_t>(ws, w.status), st, diag);
 }
 
 int loss_grad(sos_plan_s* p, int prec, const void* A, const void* pv, void* grad, void* loss, void* ws,
@@ -231,8 +236,16 @@ int sos_step(sos_plan_t p, int prec, sos_state* s, const void* pv, const sos_ste
         if (!(s->flags & SOS_STATE_BF16_CURRENT))
             SOS_CHECK(launch_cast_bf16(static_cast<const float*>(s->A), p->N, p->r, a16_cur, p->ld16, st));
         SOS_CUDA(cudaMemsetAsync(c, 0, (size_t)p->M * sizeof(float), st));
-        SOS_CHECK(use_cta_pairs() ? launch_tc_forward_pair(p, a16_cur, c, status, st)
-                                  : launch_tc_forward(p, a16_cur, c, status, st));
+        if (use_cta_pairs()) {
+            float* diag = nullptr;
+            if (use_exact_diag()) {
+                diag = at<float>(ws, w.diag);
+                SOS_CHECK(launch_diag_sumsq(a16_cur, p->ld16, p->N, p->r, diag, st));
+            }
+            SOS_CHECK(launch_tc_forward_pair(p, a16_cur, c, status, st, diag));
+        } else {
+            SOS_CHECK(launch_tc_forward(p, a16_cur, c, status, st));
+        }
         double* L = loss ? static_cast<double*>(loss) : at<double>(ws, w.loss);
         SOS_CHECK(launch_residual<float>(p, c, static_cast<const float*>(pv), resid, L, at<double>(ws, w.partials),
                                          status, 1, st));

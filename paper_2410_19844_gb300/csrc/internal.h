@@ -79,6 +79,7 @@ struct Workspace {
     size_t resid = 0;      // M residuals (float or double)
     size_t grad = 0;       // N x r gradient (float or double)
     size_t a16 = 0;        // 2 x N x ld16 bf16 copies of A, ping-pong (SOS_BF16 only)
+    size_t diag = 0;       // N floats: the diagonal of A A^T from the bf16 copy (SOS_BF16 only)
     size_t h16 = 0;        // N x ld16h bf16 H(resid)   (SOS_BF16 without the ring, SOS_FP64_TC)
     size_t ring = 0;       // S x 256 x ld16h bf16 panels of H(resid) (SOS_BF16 with the ring)
     size_t ring_flags = 0; // abort word, built and consumed counters of the ring
@@ -163,6 +164,11 @@ Workspace workspace_layout(const sos_plan_s* plan, int prec);
 // on the large workload it is about 9% slower than materialising H, and it
 // holds a few bands of panels instead of the whole N x N H.
 bool use_h_ring();
+// Whether the BF16 forward takes the diagonal of A A^T from a CUDA-core sum of
+// the bf16 squares (FP32, round to nearest) instead of the tensor-core
+// accumulator, which truncates once per 16-deep step (environment variable
+// SOS_EXACT_DIAG = 1, read once; off by default).
+bool use_exact_diag();
 // Row-block band height of the adjoint's tile list (SOS_BAND_ADJ, default 8).
 int adjoint_band();
 // The ring of H panels: G = band height, S = slots (D G for a depth of D bands,
@@ -181,6 +187,9 @@ int launch_build_idx(const sos_plan_s* plan, int32_t* idx, const uint8_t* d_S, c
                      cudaStream_t st);
 int launch_cast_bf16(const float* A, int64_t N, int64_t r, void* a16, int64_t ld16,
                      cudaStream_t st);
+// d[a] = sum_k bf16(A)[a][k]^2 from the bf16 copy, FP32 on CUDA cores (the exact
+// diagonal of the BF16 forward).
+int launch_diag_sumsq(const void* a16, int64_t ld16, int64_t N, int64_t r, float* d, cudaStream_t st);
 template <typename Tin, typename Tacc>
 int launch_simt_forward(const sos_plan_s* plan, const Tin* A, Tacc* c, int64_t batch,
                         cudaStream_t st);
@@ -213,7 +222,10 @@ int launch_tc_adjoint_update(const sos_plan_s* plan, const void* h16, const void
 
 // ---- the same on CTA pairs (kernels_tc2.cu) ---------------------------------------
 
-int launch_tc_forward_pair(const sos_plan_s* plan, const void* a16, float* c, int32_t* status, cudaStream_t st);
+// diag (N floats, or NULL): when given, the segment-sum takes the diagonal of
+// A A^T from it instead of from the tensor-core accumulator.
+int launch_tc_forward_pair(const sos_plan_s* plan, const void* a16, float* c, int32_t* status, cudaStream_t st,
+                           const float* diag = nullptr);
 int launch_tc_adjoint_pair(const sos_plan_s* plan, const void* h16, const void* a16, float* grad,
                            int32_t* status, cudaStream_t st);
 // The same two adjoints reading H(resid) from the ring in the workspace

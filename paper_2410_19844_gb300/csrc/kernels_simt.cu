@@ -62,6 +62,50 @@ __global__ void cast_bf16_kernel(const float* __restrict__ A, int64_t N, int64_t
     }
 }
 
+// Diagonal of A A^T from the bf16 copy, on CUDA cores: d[a] = sum_k bf16(A)[a][k]^2.
+// Each product is exact in FP32 (a bf16 square needs 16 significand bits); the
+// sums round to nearest.  One warp per row: each lane takes 16-byte vectors of
+// 8 bf16, four vectors in flight per iteration, and keeps 8 partial sums
+// (about r / 256 terms each), which it adds in a fixed order before a
+// fixed-order shuffle reduction; a row's sum carries at most about
+// (r / 256 + 8) 2^-24 of relative error, unbiased.
+__device__ __forceinline__ void add_squares8(const uint4& v, float (&part)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(h[q]);
+        part[2 * q] = fmaf(f.x, f.x, part[2 * q]);
+        part[2 * q + 1] = fmaf(f.y, f.y, part[2 * q + 1]);
+    }
+}
+
+__global__ void diag_sumsq_kernel(const __nv_bfloat16* __restrict__ a16, int64_t ld16, int64_t N, int64_t r,
+                                  float* __restrict__ d) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const __nv_bfloat16* x = a16 + row * ld16;
+    const uint4* xv = reinterpret_cast<const uint4*>(x);   // rows are 128-byte aligned (ld16 % 64 == 0)
+    const int64_t nvec = r / 8;                             // whole vectors of the row
+    float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int64_t v = lane;
+    for (; v + 96 < nvec; v += 128) {
+        const uint4 a = __ldg(xv + v), b = __ldg(xv + v + 32), c = __ldg(xv + v + 64), e = __ldg(xv + v + 96);
+        add_squares8(a, part);
+        add_squares8(b, part);
+        add_squares8(c, part);
+        add_squares8(e, part);
+    }
+    for (; v < nvec; v += 32) add_squares8(__ldg(xv + v), part);
+    for (int64_t j = nvec * 8 + lane; j < r; j += 32) {
+        const float f = __bfloat162float(x[j]);
+        part[j & 7] = fmaf(f, f, part[j & 7]);
+    }
+    float s = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) d[row] = s;
+}
+
 // ---- forward: upper-triangle tiles of A A^T, segment-summed into c ------------------
 // 64 x 64 tile (I, J), J >= I; 256 threads, 4 x 4 outputs each at rows
 // ty + 16 i and columns tx + 16 j; K in chunks of 16 staged in shared memory.
@@ -515,6 +559,18 @@ int launch_build_idx(const sos_plan_s* p, int32_t* idx, const uint8_t* d_S, cons
     {
         KernelScope ks_("build_idx", st);
         build_idx_kernel<<<grid, kThreads, smem, st>>>(p->n, W, p->N, p->ld_idx, d_S, d_phi, idx);
+    }
+    SOS_CUDA(cudaGetLastError());
+    return SOS_OK;
+}
+
+int launch_diag_sumsq(const void* a16, int64_t ld16, int64_t N, int64_t r, float* d, cudaStream_t st) {
+    const int64_t blocks = ceil_div(N * 32, kThreads);
+    if (blocks > INT32_MAX) return fail(SOS_E_UNSUPPORTED, "diag_sumsq: too many rows");
+    {
+        KernelScope ks_("diag_sumsq", st);
+        diag_sumsq_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(static_cast<const __nv_bfloat16*>(a16), ld16, N, r,
+                                                                 d);
     }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;

@@ -440,12 +440,13 @@ int adjoint_pair_capacity(int* pairs) {
     return per_device_value(kern, pairs, [kern, threads](int* v) -> int { return resident_pairs(kern, threads, v); });
 }
 
-int launch_tc_forward_pair(const sos_plan_s* p, const void* a16, float* c, int32_t* status, cudaStream_t st) {
+int launch_tc_forward_pair(const sos_plan_s* p, const void* a16, float* c, int32_t* status, cudaStream_t st,
+                           const float* diag) {
     using namespace tc2;
     CUtensorMap mA, mB;
     SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, BK, BM));
     SOS_CHECK(make_bf16_map(&mB, a16, p->r, p->N, p->ld16, BK, BN / 2));
-    tc::SegmentSumEpilogue epi{(int)p->N, p->dev.idx, p->ld_idx, c};
+    tc::SegmentSumEpilogue epi{(int)p->N, p->dev.idx, p->ld_idx, c, diag};
     return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), p->dev.fwd_tiles2, p->dev.num_fwd_tiles2, epi,
                                    status, st);
 }

@@ -86,6 +86,7 @@ Workspace workspace_layout(const sos_plan_s* p, int prec) {
     w.grad = take((size_t)p->N * (size_t)p->r * (prec == SOS_FP64_TC ? 4 : elt));
     if (prec == SOS_BF16) {
         w.a16 = take(2 * (size_t)p->N * (size_t)p->ld16 * 2);
+        w.diag = take((size_t)p->N * sizeof(float));
         if (use_h_ring()) {
             const RingGeometry g = ring_geometry(p);
             w.ring = take((size_t)g.slots * 256 * (size_t)p->ld16h * 2);
@@ -317,6 +318,14 @@ int adjoint_band() {
         const char* e = std::getenv("SOS_BAND_ADJ");
         const int b = e ? std::atoi(e) : 0;
         return b > 0 ? b : 8;
+    }();
+    return v;
+}
+
+bool use_exact_diag() {
+    static const bool v = [] {
+        const char* e = std::getenv("SOS_EXACT_DIAG");
+        return e && e[0] == '1';
     }();
     return v;
 }

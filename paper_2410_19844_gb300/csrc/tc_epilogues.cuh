@@ -43,6 +43,8 @@ __device__ __forceinline__ int stage_swz(int i) { return ((i & 3) << 3) | ((i >>
 __device__ __forceinline__ int stage_idx(int i, int j) { return i * 32 + (j ^ stage_swz(i)); }
 
 // Forward: c[idx(a, b)] += w G_ab for b >= a (w = 1 on the diagonal, 2 above).
+// With diag given, G_aa comes from diag[a] (a CUDA-core sum of the bf16
+// squares, rounded to nearest) instead of the accumulator.
 // The warp walks the 32 x 32 block in 4 x 8 patches (lane = 8 dr + dc: row
 // 4 (t / 4) + dr, column 8 (t % 4) + dc at step t): entries (a, b) and
 // (a + 1, b - 1) often share the monomial a + b, so a compact patch's 32
@@ -55,6 +57,7 @@ struct SegmentSumEpilogue {
     const int32_t* idx;
     int64_t ld_idx;
     float* c;
+    const float* diag = nullptr;
 
     __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
         if (a0 >= N || b0 >= N || b0 + 31 < a0) return;
@@ -69,8 +72,9 @@ struct SegmentSumEpilogue {
         for (int t = 0; t < 32; ++t) {
             if (g[t] >= 0) {
                 const int i = 4 * (t >> 2) + dr, j = 8 * (t & 3) + dc;
-                const float v = stage[stage_idx(i, j)];
-                atomicAdd(c + g[t], a0 + i == b0 + j ? v : 2.0f * v);
+                const bool on_diag = a0 + i == b0 + j;
+                const float v = (diag != nullptr && on_diag) ? __ldg(diag + a0 + i) : stage[stage_idx(i, j)];
+                atomicAdd(c + g[t], on_diag ? v : 2.0f * v);
             }
         }
     }
