@@ -114,6 +114,12 @@ struct DeviceTables {
     int2* fwd_tiles2 = nullptr;  // the same in 256 x 256 tiles, for CTA pairs
     int2* adj_tiles2 = nullptr;  // entries with y < 0: narrow tiles, 128 columns from 128 (-y - 1)
     int32_t* panel_tiles = nullptr;  // per 256-row block: the adjoint tiles (of adj_tiles2) that read it
+    // units of two 256 x 256 tiles sharing a column block, for clusters of two
+    // pairs that multicast the B operand (a second tile with x < 0 stands in)
+    int2* fwd_units = nullptr;
+    int2* adj_units = nullptr;
+    int num_fwd_units = 0;
+    int num_adj_units = 0;
     int num_fwd_tiles2 = 0;
     int num_adj_tiles2 = 0;
     // pair lists of the Gram identity, grouped by coefficient (built on demand):
@@ -164,6 +170,10 @@ Workspace workspace_layout(const sos_plan_s* plan, int prec);
 // on the large workload it is about 9% slower than materialising H, and it
 // holds a few bands of panels instead of the whole N x N H.
 bool use_h_ring();
+// Whether the CTA-pair contractions run in clusters of two pairs that share
+// the B operand by TMA multicast (environment variable SOS_MCAST = 1, read
+// once; only with the CTA-pair kernels, not with the H ring).
+bool use_mcast();
 // Whether the BF16 forward takes the diagonal of A A^T from a CUDA-core sum of
 // the bf16 squares (FP32, round to nearest) instead of the tensor-core
 // accumulator, which truncates once per 16-deep step (environment variable

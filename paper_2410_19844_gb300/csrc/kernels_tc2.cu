@@ -22,6 +22,15 @@
 // panels while the MMAs run (h_ring.cuh):
 //   warps 6-7 (both CTAs)        : builders of the CTA's share of later panels
 //
+// With MC, a cluster of four CTAs runs two pairs on two tiles that share the
+// B operand (the same column block): pair 0's CTAs load each half of B once and
+// multicast it into both pairs' shared memory, which cuts the operand bytes each
+// SM pulls from L2 by a quarter.  A stage is then refilled only when both pairs'
+// MMAs are done with it: every empty barrier counts both leaders' commits.
+// Tiles come in units of two (one per pair); a unit whose second tile has
+// x < 0 runs a copy of the first tile (row block -1 - x) whose results are
+// dropped.
+//
 // A tile entry (x, y) is row block x of 256 and column block y of 256.  An
 // entry with y < 0 is a narrow tile: columns 128 (-y - 1) onwards, 128 wide,
 // computed with N = 128 MMAs (each CTA supplies 64 columns of B).  The tile
@@ -72,13 +81,14 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 __host__ __device__ constexpr int threads_of(bool ring) { return ring ? RING_THREADS : THREADS; }
 
-template <bool B_MN_MAJOR, class Epilogue, bool RING = false>
+template <bool B_MN_MAJOR, class Epilogue, bool RING = false, bool MC = false>
 __global__ void __launch_bounds__(threads_of(RING), 1)
 tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int nkb,
                     const int2* __restrict__ tiles, int num_tiles, Epilogue epi, int32_t* __restrict__ status,
                     RingArgs ring) {
     static_assert(!(Epilogue::kSegmented && B_MN_MAJOR), "segmented K runs with K-major operands only");
     static_assert(!(Epilogue::kSegmented && RING), "the H ring serves the adjoint only");
+    static_assert(!(MC && (RING || Epilogue::kSegmented)), "multicast runs plain tiles only");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* base = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -95,14 +105,20 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
     float* epi_stage = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + BAR_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_ctarank();
+    const uint32_t crank = cluster_ctarank();
+    const uint32_t rank = crank & 1u;            // rank within the CTA pair
+    const uint32_t lead_rank = crank & ~1u;      // cluster rank of this pair's leader
     const bool leader = rank == 0;
-    const int pair = blockIdx.x >> 1, num_pairs = gridDim.x >> 1;
+    const int pc = MC ? (int)(crank >> 1) : 0;   // pair within the cluster
+    // Work items: tiles, or with MC units of one tile per pair of the cluster.
+    const int pair = MC ? (int)(blockIdx.x >> 2) : (int)(blockIdx.x >> 1);
+    const int num_pairs = MC ? (int)(gridDim.x >> 2) : (int)(gridDim.x >> 1);
+    auto tile_at = [&](int t) { return MC ? tiles[2 * t + pc] : tiles[t]; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], MC ? 2 : 1);     // with MC both pairs' leaders release a stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -131,9 +147,10 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
         int64_t issued = 0;
         bool ok = true;
         for (int t = pair; t < num_tiles && ok; t += num_pairs) {
-            const int2 tile = tiles[t];
+            const int2 tile = tile_at(t);
             const bool narrow = tile.y < 0;
-            int arow = tile.x * PAIR_M + (int)rank * BM;
+            const int tx = (MC && tile.x < 0) ? -1 - tile.x : tile.x;
+            int arow = tx * PAIR_M + (int)rank * BM;
             if constexpr (RING) {
                 // the tile's rows of H are panel tile.x, in its ring slot
                 if (tile.x >= ring.first_panel) {
@@ -155,7 +172,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                     break;
                 }
                 if (leader) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
-                const uint32_t bar = mapa_shared(smem_u32(&full[s]), 0);
+                const uint32_t bar = mapa_shared(smem_u32(&full[s]), lead_rank);
 #pragma unroll
                 for (int at = 0; at < KATOMS; ++at) {
                     int kx = (kb + at) * BK;            // beyond K: zero fill, still counted
@@ -170,7 +187,20 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                         bc = epi.seg_brow(tile, seg) + (int)rank * (BN / 2);
                     }
                     tma_load_2d_pair(sA + s * A_BYTES + at * ATOM_A, &mapA, bar, kx, ar);
-                    if (B_MN_MAJOR) {
+                    if constexpr (MC) {
+                        // pair 0 loads B for both pairs; pair 1's bytes arrive on its own leader
+                        const uint16_t mask = (uint16_t)((1u << crank) | (1u << (crank + 2)));
+                        if (pc == 0) {
+                            if (B_MN_MAJOR) {
+#pragma unroll
+                                for (int j = 0; j < BN / 2 / 64; ++j)
+                                    tma_load_2d_pair_multicast(sB + s * B_BYTES + at * ATOM_B + j * (64 * BK * 2),
+                                                               &mapB, bar, bcol + 64 * j, kx, mask);
+                            } else {
+                                tma_load_2d_pair_multicast(sB + s * B_BYTES + at * ATOM_B, &mapB, bar, kx, bc, mask);
+                            }
+                        }
+                    } else if (B_MN_MAJOR) {
 #pragma unroll
                         for (int j = 0; j < BN / 2 / 64; ++j)
                             tma_load_2d_pair(sB + s * B_BYTES + at * ATOM_B + j * (64 * BK * 2), &mapB, bar,
@@ -204,10 +234,10 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
         int it = 0;
         bool ok = true;
         // the next tile's entry is loaded one tile ahead, off the issue path
-        int2 next = pair < num_tiles ? tiles[pair] : make_int2(0, 0);
+        int2 next = pair < num_tiles ? tile_at(pair) : make_int2(0, 0);
         for (int t = pair; t < num_tiles && ok; t += num_pairs, ++it) {
             const int2 tile = next;
-            if (t + num_pairs < num_tiles) next = tiles[t + num_pairs];
+            if (t + num_pairs < num_tiles) next = tile_at(t + num_pairs);
             const int buf = it & 1;
             const uint32_t tph = (uint32_t)(it >> 1) & 1u;
             if (*err || !mbar_wait(&tempty[buf], tph ^ 1u, WAIT_LIMIT_NS)) {
@@ -238,26 +268,26 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                         umma_bf16_pair(dtm, ad, bd, idesc, (kb | at | kk) != 0 ? 1u : 0u);
                     }
                 }
-                umma_commit_pair_multicast(&empty[s], 0x3);
+                umma_commit_pair_multicast(&empty[s], MC ? 0xF : 0x3);
                 if (++s == STAGES) {
                     s = 0;
                     ph ^= 1u;
                 }
             }
             if (!ok) break;
-            umma_commit_pair_multicast(&tfull[buf], 0x3);
+            umma_commit_pair_multicast(&tfull[buf], (uint16_t)(0x3u << lead_rank));
         }
         if (!ok) {
             *err = 1;
             atomicCAS(status, 0, SOS_E_TIMEOUT);
             if constexpr (RING) atomicExch(ring.abort_word(), 1u);
         }
-        umma_commit_pair_multicast(drain, 0x1);
+        umma_commit_pair_multicast(drain, (uint16_t)(1u << lead_rank));
         mbar_wait(drain, 0, WAIT_LIMIT_NS);
     } else if (warp >= 2 && warp < 6) {
         // ---------------- epilogue (both CTAs) ----------------
         const int q = warp & 3;
-        const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), 0);
+        const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), lead_rank);
         int it = 0;
         for (int t = pair; t < num_tiles; t += num_pairs, ++it) {
             const int buf = it & 1;
@@ -272,7 +302,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 break;
             }
             tc_fence_after();
-            const int2 tile = tiles[t];
+            const int2 tile = tile_at(t);
             if constexpr (RING) {
                 // the tile's MMAs are done, so both CTAs' loads of its panel have landed
                 if (leader && warp == 2 && lane == 0) red_release_gpu_add(ring.consumed(tile.x), 1u);
@@ -280,7 +310,8 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
             float* stage = epi_stage + (warp - 2) * STAGE_FLOATS;
             const int row0 = tile.x * PAIR_M + (int)rank * BM + q * 32;
             const int col0 = tile.y < 0 ? (-tile.y - 1) * (BN / 2) : tile.y * BN;
-            const int nch = tile.y < 0 ? BN / 64 : BN / 32;
+            // a unit's stand-in tile (x < 0, with MC) computes but stores nothing
+            const int nch = (MC && tile.x < 0) ? 0 : (tile.y < 0 ? BN / 64 : BN / 32);
 #pragma unroll 1
             for (int ch = 0; ch < nch; ++ch) {
                 uint32_t v[32];
@@ -368,11 +399,11 @@ namespace {
 // every CTA of the grid is resident at once (the H ring's builders and
 // producers wait on one another across CTAs).
 void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cudaStream_t st, int threads,
-                        bool cooperative) {
+                        bool cooperative, int cluster = 2) {
     using namespace tc2;
     cfg = {};
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     attr[1].id = cudaLaunchAttributeCooperative;
@@ -384,8 +415,8 @@ void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cuda
     cfg.numAttrs = cooperative ? 2 : 1;
 }
 
-// How many CTA pairs of `kern` fit on the current GPU at once.
-int resident_pairs(const void* kern, int threads, int* out) {
+// How many clusters (of two CTAs by default) of `kern` fit on the current GPU at once.
+int resident_pairs(const void* kern, int threads, int* out, int cluster = 2) {
     using namespace tc2;
     SOS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     int dev = 0, sms = 0;
@@ -393,33 +424,37 @@ int resident_pairs(const void* kern, int threads, int* out) {
     SOS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];
-    pair_launch_config(cfg, attr, 0, threads, false);
-    cfg.gridDim = dim3(sms);
+    pair_launch_config(cfg, attr, 0, threads, false, cluster);
+    cfg.gridDim = dim3(sms / cluster * cluster);
     int clusters = 0;
     SOS_CUDA(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
-    if (clusters < 1) return fail(SOS_E_UNSUPPORTED, "CTA pairs: no cluster of two fits on this GPU");
+    if (clusters < 1) return fail(SOS_E_UNSUPPORTED, "CTA pairs: no cluster fits on this GPU");
     *out = clusters;
     return SOS_OK;
 }
 
-template <bool B_MN, class Epi, bool RING = false>
+// With MC, `tiles` holds units of two tiles (num_tiles units) and the grid is
+// made of clusters of four CTAs (two pairs).
+template <bool B_MN, class Epi, bool RING = false, bool MC = false>
 int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
                      const Epi& epi, int32_t* status, cudaStream_t st, const tc::RingArgs& ring = tc::RingArgs{}) {
     using namespace tc2;
-    auto kern = tc_gemm_pair_kernel<B_MN, Epi, RING>;
+    auto kern = tc_gemm_pair_kernel<B_MN, Epi, RING, MC>;
     const int threads = threads_of(RING);
+    constexpr int cluster = MC ? 4 : 2;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];
-    pair_launch_config(cfg, attr, st, threads, RING);
-    // every pair resident at once: the tile loop assumes it
-    int max_pairs = 0;
-    SOS_CHECK(per_device_value((const void*)kern, &max_pairs,
-                               [kern, threads](int* v) -> int { return resident_pairs((const void*)kern, threads, v); }));
+    pair_launch_config(cfg, attr, st, threads, RING, cluster);
+    // every cluster resident at once: the tile loop assumes it
+    int max_clusters = 0;
+    SOS_CHECK(per_device_value((const void*)kern, &max_clusters, [kern, threads](int* v) -> int {
+        return resident_pairs((const void*)kern, threads, v, cluster);
+    }));
     if (num_tiles <= 0) return SOS_OK;
     // the ring's producers wait for every CTA's builders: the whole persistent
     // grid runs even when there are fewer tiles than pairs
-    const int pairs = RING ? max_pairs : (num_tiles < max_pairs ? num_tiles : max_pairs);
-    cfg.gridDim = dim3(2 * pairs);
+    const int clusters = RING ? max_clusters : (num_tiles < max_clusters ? num_tiles : max_clusters);
+    cfg.gridDim = dim3(cluster * clusters);
     const char* name = Epi::kName;
     if constexpr (RING) name = Epi::kRingName;
     {
@@ -447,6 +482,9 @@ int launch_tc_forward_pair(const sos_plan_s* p, const void* a16, float* c, int32
     SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, BK, BM));
     SOS_CHECK(make_bf16_map(&mB, a16, p->r, p->N, p->ld16, BK, BN / 2));
     tc::SegmentSumEpilogue epi{(int)p->N, p->dev.idx, p->ld_idx, c, diag};
+    if (use_mcast())
+        return launch_pair_gemm<false, tc::SegmentSumEpilogue, false, true>(
+            mA, mB, (int)ceil_div(p->r, BK), p->dev.fwd_units, p->dev.num_fwd_units, epi, status, st);
     return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), p->dev.fwd_tiles2, p->dev.num_fwd_tiles2, epi,
                                    status, st);
 }
@@ -473,6 +511,9 @@ int launch_tc_adjoint_update_pair(const sos_plan_s* p, const void* h16, const vo
     epi.v = v;
     epi.a16_next = static_cast<__nv_bfloat16*>(a16_next);
     epi.ld16 = p->ld16;
+    if (use_mcast())
+        return launch_pair_gemm<true, tc::UpdateEpilogue, false, true>(
+            mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_units, p->dev.num_adj_units, epi, status, st);
     return launch_pair_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles2, p->dev.num_adj_tiles2, epi,
                                   status, st);
 }
@@ -547,6 +588,9 @@ int launch_tc_adjoint_pair(const sos_plan_s* p, const void* h16, const void* a16
     SOS_CHECK(make_bf16_map(&mH, h16, p->N, p->N, p->ld16h, BK, BM));
     SOS_CHECK(make_bf16_map(&mA, a16, p->r, p->N, p->ld16, 64, BK));
     tc::StoreEpilogue epi{(int)p->N, (int)p->r, p->r, 2.0f, grad};
+    if (use_mcast())
+        return launch_pair_gemm<true, tc::StoreEpilogue, false, true>(
+            mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_units, p->dev.num_adj_units, epi, status, st);
     return launch_pair_gemm<true>(mH, mA, (int)ceil_div(p->N, BK), p->dev.adj_tiles2, p->dev.num_adj_tiles2, epi,
                                   status, st);
 }

@@ -184,6 +184,8 @@ int sos_plan_destroy(sos_plan_t p) {
         cudaFree(p->dev.fwd_tiles2);
         cudaFree(p->dev.adj_tiles2);
         cudaFree(p->dev.panel_tiles);
+        cudaFree(p->dev.fwd_units);
+        cudaFree(p->dev.adj_units);
         cudaFree(p->dev.pair_ptr);
         cudaFree(p->dev.pair_pos);
         cudaFree(p->dev.form_rows);
@@ -256,6 +258,39 @@ namespace sos {
 // i.e. J >= floor(I / 2).  The adjoint covers N x r in tiles of 128 x 256.
 // Both lists walk bands of row blocks so that the CTAs running at the same
 // time share operand panels in L2.
+// Units of two tiles sharing the column block y: consecutive row blocks of
+// `rows` pair up; an odd one out gets a stand-in (x = -1 - x) that recomputes
+// it and stores nothing.
+static void push_units(std::vector<int2>& out, const std::vector<int>& rows, int y) {
+    for (size_t k = 0; k < rows.size(); k += 2) {
+        out.push_back(make_int2(rows[k], y));
+        out.push_back(k + 1 < rows.size() ? make_int2(rows[k + 1], y) : make_int2(-1 - rows[k], y));
+    }
+}
+
+static void make_units(const sos_plan_s* p, std::vector<int2>& fwd_u, std::vector<int2>& adj_u) {
+    const int TP = (int)ceil_div(p->N, 256), TK = (int)ceil_div(p->r, 256);
+    const int bf = 8, ba = adjoint_band();
+    std::vector<int> rows;
+    for (int i0 = 0; i0 < TP; i0 += bf) {
+        const int i1 = std::min(TP, i0 + bf);
+        for (int J = i0; J < TP; ++J) {
+            rows.clear();
+            for (int I = i0; I < i1; ++I)
+                if (J >= I) rows.push_back(I);
+            push_units(fwd_u, rows, J);
+        }
+    }
+    for (int i0 = 0; i0 < TP; i0 += ba) {
+        const int i1 = std::min(TP, i0 + ba);
+        for (int K = 0; K < TK; ++K) {
+            rows.clear();
+            for (int I = i0; I < i1; ++I) rows.push_back(I);
+            push_units(adj_u, rows, K);
+        }
+    }
+}
+
 static void make_tiles(const sos_plan_s* p, int pairs, std::vector<int2>& fwd, std::vector<int2>& adj,
                        std::vector<int2>& fwd2, std::vector<int2>& adj2) {
     const int TI = (int)ceil_div(p->N, 128), TJ = (int)ceil_div(p->N, 256);
@@ -322,6 +357,14 @@ int adjoint_band() {
     return v;
 }
 
+bool use_mcast() {
+    static const bool v = [] {
+        const char* e = std::getenv("SOS_MCAST");
+        return e && e[0] == '1';
+    }();
+    return v && use_cta_pairs() && !use_h_ring();
+}
+
 bool use_exact_diag() {
     static const bool v = [] {
         const char* e = std::getenv("SOS_EXACT_DIAG");
@@ -384,9 +427,17 @@ int ensure_device(sos_plan_s* p) {
     // adjoint tiles per 256-row panel (the ring's slot-release counts)
     std::vector<int32_t> panel_tiles((size_t)ceil_div(p->N, 256), 0);
     for (const int2& tl : adj2) panel_tiles[tl.x]++;
+    std::vector<int2> fwd_u, adj_u;
+    if (use_mcast()) make_units(p, fwd_u, adj_u);
     uint8_t* d_S = nullptr;
     int32_t* d_phi = nullptr;
     cudaError_t e = cudaMalloc(&t.idx, idx_bytes);
+    if (e == cudaSuccess && !fwd_u.empty()) e = cudaMalloc(&t.fwd_units, fwd_u.size() * sizeof(int2));
+    if (e == cudaSuccess && !adj_u.empty()) e = cudaMalloc(&t.adj_units, adj_u.size() * sizeof(int2));
+    if (e == cudaSuccess && !fwd_u.empty())
+        e = cudaMemcpy(t.fwd_units, fwd_u.data(), fwd_u.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !adj_u.empty())
+        e = cudaMemcpy(t.adj_units, adj_u.data(), adj_u.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&t.panel_tiles, panel_tiles.size() * sizeof(int32_t));
     if (e == cudaSuccess)
         e = cudaMemcpy(t.panel_tiles, panel_tiles.data(), panel_tiles.size() * sizeof(int32_t),
@@ -427,12 +478,16 @@ int ensure_device(sos_plan_s* p) {
         cudaFree(t.fwd_tiles2);
         cudaFree(t.adj_tiles2);
         cudaFree(t.panel_tiles);
+        cudaFree(t.fwd_units);
+        cudaFree(t.adj_units);
         return rc;
     }
     t.num_fwd_tiles = (int)fwd.size();
     t.num_adj_tiles = (int)adj.size();
     t.num_fwd_tiles2 = (int)fwd2.size();
     t.num_adj_tiles2 = (int)adj2.size();
+    t.num_fwd_units = (int)(fwd_u.size() / 2);
+    t.num_adj_units = (int)(adj_u.size() / 2);
     p->dev = t;
     return SOS_OK;
 }

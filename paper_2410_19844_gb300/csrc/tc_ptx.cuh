@@ -198,6 +198,19 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m
         : "memory");
 }
 
+// The same load written into this CTA's shared memory and into the CTAs of
+// cta_mask at the same offset (TMA multicast within the cluster).  With the
+// barrier given in a pair leader, each destination's bytes are counted on the
+// barrier at that offset in its own pair's leader.
+__device__ __forceinline__ void tma_load_2d_pair_multicast(void* dst, const CUtensorMap* map, uint32_t bar_cluster_addr,
+                                                           int x, int y, uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster_addr), "r"(x), "r"(y),
+        "h"(cta_mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_slot)),
                  "r"(ncols)
