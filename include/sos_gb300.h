@@ -364,7 +364,7 @@ int sos_solve(sos_plan_t plan, const double* p64, double* A, const sos_solve_opt
 
 /* A group steps up to `capacity` independent problems, each with its own plan
  * (any n, 2d; r must equal N) and buffers, FP32 or FP64 on CUDA cores.  One
- * group step runs four kernels whose work lists cover every active problem
+ * group step runs three kernels whose work lists cover every active problem
  * (64 x 64 tiles of every A A^T, coefficient chunks, tiles of every 2 H A with
  * the optimiser update fused), so large and small problems share the GPU.
  * No result depends on which other problems share the group: a problem's

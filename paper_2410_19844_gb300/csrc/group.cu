@@ -1,18 +1,19 @@
 // Grouped steps over many independent problems (serving).
 //
 // A group holds up to `capacity` problems, each with its own plan (n, 2d),
-// r = N, and its own buffers.  One step of the group runs four kernels whose
+// r = N, and its own buffers.  One step of the group runs three kernels whose
 // work lists span every active problem, so large and small problems share the
 // GPU the way a grouped GEMM shares it:
 //   forward   64 x 64 tiles of G = A A^T on or above the diagonal, written
 //             to the problem's G (no atomics)                  (Eq. 1)
 //   residual  chunks of 2048 coefficients: c_g is gathered from G through the
-//             plan's pair lists, r = c - p, partial sums of ||r||^2, ||p||^2
+//             plan's pair lists, r = c - p, partial sums of ||r||^2, ||p||^2;
+//             one thread also advances the group's step counter, which the
+//             forward reads before it and the adjoint (as counter - 1) after it
 //   adjoint   64 x 64 tiles of grad = 2 H(r) A with H gathered from r through
 //             the index table, fused with the GD / Adam update (Sec. 3); the
 //             operand A is read from one buffer of a ping-pong pair and the
 //             update written to the other
-//   advance   the group's step counter += 1
 // Every result is computed by one thread in a fixed order, so a problem's
 // iterates do not depend on which other problems share the group.  The work
 // lists and counters live in device memory, so the captured graph of K steps
@@ -200,8 +201,11 @@ group_forward_df(const int* __restrict__ counts, const Item* __restrict__ items,
 template <typename T>
 __global__ void __launch_bounds__(kT)
 group_residual(const int* __restrict__ counts, const Item* __restrict__ items, int cap,
-               const Inst<T>* __restrict__ insts) {
+               const Inst<T>* __restrict__ insts, long long* __restrict__ step) {
     __shared__ double red[2][kT / 32];
+    // the forward of this step has read the counter and the adjoint reads it
+    // after this kernel: advancing it here saves a launch per step
+    if (blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
     const int n_items = counts[1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
@@ -259,7 +263,7 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
     __shared__ Tc Bs[16][64];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int n_items = counts[2];
-    const long long now = *step;
+    const long long now = *step - 1;     // the residual kernel has advanced the counter
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
         const Item it = items[2 * cap + w];
         const Inst<T>& in = insts[it.inst];
@@ -334,7 +338,6 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
     }
 }
 
-__global__ void group_advance(long long* step) { *step += 1; }
 
 template <typename T>
 __global__ void group_collect(const Inst<T>* __restrict__ insts, int capacity, double* __restrict__ out) {
@@ -490,7 +493,7 @@ int launch_step(sos_group_s* g, cudaStream_t st) {
     }
     {
         KernelScope ks_("group_residual", st);
-        group_residual<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts);
+        group_residual<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step);
     }
     {
         KernelScope ks_("group_adjoint", st);
@@ -503,10 +506,6 @@ int launch_step(sos_group_s* g, cudaStream_t st) {
         else
             group_adjoint<T, T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
                                                         g->optimizer, g->b1, g->b2, g->eps);
-    }
-    {
-        KernelScope ks_("group_advance", st);
-        group_advance<<<1, 1, 0, st>>>(g->d_step);
     }
     SOS_CUDA(cudaGetLastError());
     return SOS_OK;
@@ -676,7 +675,7 @@ int sos_group_sync(sos_group_t g, void* stream) {
     return SOS_OK;
 }
 
-// Runs `steps` steps of every active problem: a graph of steps x 4 kernels,
+// Runs `steps` steps of every active problem: a graph of steps x 3 kernels,
 // captured on the group's private stream the first time and replayed after,
 // ordered after and before the caller's stream with events.
 int sos_group_run(sos_group_t g, int steps, void* stream) {
