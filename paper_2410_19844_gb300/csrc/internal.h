@@ -84,13 +84,31 @@ struct Workspace {
     size_t ring = 0;       // S x 256 x ld16h bf16 panels of H(resid) (SOS_BF16 with the ring)
     size_t ring_flags = 0; // abort word, built and consumed counters of the ring
     size_t resid32 = 0;    // M float residuals         (SOS_FP64_TC only)
-    size_t slices = 0;     // kMaxSlices x NP x ld16 bf16 slices of A, NP = N rounded up to 256 (SOS_FP64_TC)
+    size_t slices = 0;     // max_slices x NP slice matrices of A, NP = N rounded up to 256 (SOS_FP64_TC)
     size_t ex = 0;         // N int32 row exponents     (SOS_FP64_TC only)
     size_t total = 0;
 };
 
-constexpr int kMaxSlices = 8;     // SOS_FP64_TC: 5-bit slices of A
+constexpr int kMaxSlices = 8;     // SOS_FP64_TC: 5-bit slices of A (the count the API takes)
 constexpr int kSliceBits = 5;
+constexpr int kMaxSlices8 = 10;   // E4M3 slices: 4-bit digits, ceil(5 s / 4) of them for s 5-bit slices
+constexpr int kMaxSlicePairs = 36; // pairs (i <= j) with i + j below kMaxSlices8 (30), rounded up
+
+// How SOS_FP64_TC cuts A into slices: bf16 slices of 5-bit digits (|d| <= 31),
+// or with SOS_SLICE_FP8 = 1 E4M3 slices of 4-bit digits (|d| <= 15, exact in
+// E4M3's three fraction bits), whose products run at twice the K per byte.
+struct SliceFormat {
+    bool fp8 = false;
+    int bits = kSliceBits;       // bits per digit
+    int dmax = 31;               // largest digit magnitude
+    int max_slices = kMaxSlices;
+    int64_t ld = 0;              // row stride of a slice matrix in elements (bf16) or bytes (E4M3)
+    int elem_bytes = 2;
+    // slices of this format that carry at least the bits of s 5-bit slices
+    int slices_for(int s) const { return (kSliceBits * s + bits - 1) / bits; }
+    // every inner sum of digit products, r dmax^2, stays below 2^24 (exact in FP32)
+    bool exact_for(int64_t r) const { return r * dmax * dmax < ((int64_t)1 << 24); }
+};
 
 // SOS_FP64_TC with r 31^2 k < 2^24 (k >= 2): slice products of one order summed
 // in one accumulator, as the segments sa[s] x sb[s] of one product (symmetric:
@@ -136,9 +154,9 @@ struct DeviceTables {
     // the stacked coordinates, ordered by i + j; the pairs with i + j < s are
     // the first slice_tile_count[s] entries
     int2* slice_tiles2 = nullptr;
-    int slice_tile_count[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    int slice_pairs = 0;                // pairs (i <= j) with i + j < kMaxSlices
-    int slice_pair_offset[37] = {0};    // tiles of the u-th pair: [offset[u], offset[u + 1])
+    int slice_tile_count[kMaxSlices8 + 1] = {0};
+    int slice_pairs = 0;                // pairs (i <= j) with i + j < the format's max_slices
+    int slice_pair_offset[kMaxSlicePairs + 1] = {0};  // tiles of the u-th pair: [offset[u], offset[u + 1])
     // grouped form (r 31^2 2 < 2^24): groups by order, tiles (g * TP + I, J)
     // with J >= I; groups of order < s own the first slice_tile_count[s] tiles
     SliceGroup* slice_groups = nullptr;
@@ -179,6 +197,11 @@ bool use_mcast();
 // accumulator, which truncates once per 16-deep step (environment variable
 // SOS_EXACT_DIAG = 1, read once; off by default).
 bool use_exact_diag();
+// Whether SOS_FP64_TC slices A into E4M3 bytes of 4-bit digits instead of
+// bf16 5-bit digits (environment variable SOS_SLICE_FP8 = 1, read once).
+bool use_slice_fp8();
+// The slice format of SOS_FP64_TC for this plan.
+SliceFormat slice_format(const sos_plan_s* plan);
 // Row-block band height of the adjoint's tile list (SOS_BAND_ADJ, default 8).
 int adjoint_band();
 // The ring of H panels: G = band height, S = slots (D G for a depth of D bands,
@@ -263,16 +286,19 @@ int core_loss_grad(sos_plan_s* plan, int prec, const void* A, const void* p, voi
 
 // ---- SOS_FP64_TC (slices.cu, kernels_tc2.cu) ----------------------------------------
 
-// c (FP64, zeroed here) = c(A) from `slices` 5-bit slices of A on tensor cores;
-// also leaves the bf16 copy of A in the workspace's a16.
+// c (FP64, zeroed here) = c(A) from slices of A on tensor cores, as many as
+// carry the bits of `slices` 5-bit slices in the plan's slice format; also
+// leaves the bf16 copy of A in the workspace's a16.
 int forward_tc64(sos_plan_s* plan, const double* A, void* ws, double* c, int slices, cudaStream_t st);
-// Every slice pair of the stacked slices S (slice i in rows i * NP ..) listed in
-// `tiles` (stacked 256 x 256 tile coordinates), in one launch.
-int launch_tc_slices_pair(const sos_plan_s* plan, const void* S, int64_t NP, const int2* tiles, int num_tiles,
-                          const int32_t* ex, double* c, int32_t* status, cudaStream_t st);
+// Every slice pair of the stacked slices S (slice i in rows i * NP .., in format
+// f) listed in `tiles` (stacked 256 x 256 tile coordinates), in one launch.
+int launch_tc_slices_pair(const sos_plan_s* plan, const SliceFormat& f, const void* S, int64_t NP,
+                          const int2* tiles, int num_tiles, const int32_t* ex, double* c, int32_t* status,
+                          cudaStream_t st);
 // The grouped form: `groups` is a device array of SliceGroup.
-int launch_tc_slice_groups_pair(const sos_plan_s* plan, const void* S, int64_t NP, const int2* tiles, int num_tiles,
-                                const void* groups, const int32_t* ex, double* c, int32_t* status, cudaStream_t st);
+int launch_tc_slice_groups_pair(const sos_plan_s* plan, const SliceFormat& f, const void* S, int64_t NP,
+                                const int2* tiles, int num_tiles, const void* groups, const int32_t* ex, double* c,
+                                int32_t* status, cudaStream_t st);
 int launch_update_mixed(int64_t N, int64_t r, double* A, float* m, float* v, const float* grad, int optimizer,
                         int64_t t, double lr, double b1, double b2, double eps, cudaStream_t st);
 

@@ -247,6 +247,26 @@ int make_bf16_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t out
     return SOS_OK;
 }
 
+// uint8 matrix (the E4M3 slices) of `outer` rows x `inner` bytes, row stride
+// ld bytes, 128-byte swizzle, zero fill outside the matrix.
+int make_u8_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_inner,
+                uint32_t box_outer) {
+    using namespace tc;
+    auto fn = encode_fn();
+    if (!fn) return fail(SOS_E_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld & 15))
+        return fail(SOS_E_INVALID, "tensor map: base or row stride not 16-byte aligned");
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SOS_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return SOS_OK;
+}
+
 namespace tc {
 
 template <bool B_MN, class Epi>

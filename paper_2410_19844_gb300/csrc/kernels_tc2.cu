@@ -31,6 +31,10 @@
 // x < 0 runs a copy of the first tile (row block -1 - x) whose results are
 // dropped.
 //
+// With F8 the operands are E4M3 bytes (the 4-bit slices of SOS_FP64_TC): the
+// shared-memory layout is the same byte for byte (128-byte rows, so an atom is
+// 128 K elements instead of 64) and each MMA is kind::f8f6f4 with K = 32.
+//
 // A tile entry (x, y) is row block x of 256 and column block y of 256.  An
 // entry with y < 0 is a narrow tile: columns 128 (-y - 1) onwards, 128 wide,
 // computed with N = 128 MMAs (each CTA supplies 64 columns of B).  The tile
@@ -81,7 +85,7 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 __host__ __device__ constexpr int threads_of(bool ring) { return ring ? RING_THREADS : THREADS; }
 
-template <bool B_MN_MAJOR, class Epilogue, bool RING = false, bool MC = false>
+template <bool B_MN_MAJOR, class Epilogue, bool RING = false, bool MC = false, bool F8 = false>
 __global__ void __launch_bounds__(threads_of(RING), 1)
 tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int nkb,
                     const int2* __restrict__ tiles, int num_tiles, Epilogue epi, int32_t* __restrict__ status,
@@ -89,6 +93,8 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
     static_assert(!(Epilogue::kSegmented && B_MN_MAJOR), "segmented K runs with K-major operands only");
     static_assert(!(Epilogue::kSegmented && RING), "the H ring serves the adjoint only");
     static_assert(!(MC && (RING || Epilogue::kSegmented)), "multicast runs plain tiles only");
+    static_assert(!(F8 && (B_MN_MAJOR || RING || MC)), "E4M3 operands are K-major slices only");
+    constexpr int BKE = F8 ? 2 * BK : BK;        // K elements of one 128-byte atom
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* base = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -175,14 +181,14 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 const uint32_t bar = mapa_shared(smem_u32(&full[s]), lead_rank);
 #pragma unroll
                 for (int at = 0; at < KATOMS; ++at) {
-                    int kx = (kb + at) * BK;            // beyond K: zero fill, still counted
+                    int kx = (kb + at) * BKE;           // beyond K: zero fill, still counted
                     int ar = arow, bc = bcol;
                     if constexpr (Epilogue::kSegmented) {
                         // atom q of the tile: K block q % nkb of segment q / nkb; past the
                         // last segment, a block beyond K (zero fill)
                         const int q = kb + at;
                         const int seg = q < nkbt ? q / nkb : 0;
-                        kx = q < nkbt ? (q - seg * nkb) * BK : nkb * BK;
+                        kx = q < nkbt ? (q - seg * nkb) * BKE : nkb * BKE;
                         ar = epi.seg_arow(tile, seg) + (int)rank * BM;
                         bc = epi.seg_brow(tile, seg) + (int)rank * (BN / 2);
                     }
@@ -227,8 +233,10 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                 mbar_wait(&full[i % STAGES], (uint32_t)((i / STAGES) & 1), WAIT_LIMIT_NS);
     } else if (warp == 1 && lane == 0 && leader) {
         // ---------------- MMA issuer (leader) ----------------
-        constexpr uint32_t idesc_full = idesc_bf16_f32(PAIR_M, BN, 0, B_MN_MAJOR ? 1 : 0);
-        constexpr uint32_t idesc_narrow = idesc_bf16_f32(PAIR_M, BN / 2, 0, B_MN_MAJOR ? 1 : 0);
+        constexpr uint32_t idesc_full =
+            F8 ? idesc_e4m3_f32(PAIR_M, BN) : idesc_bf16_f32(PAIR_M, BN, 0, B_MN_MAJOR ? 1 : 0);
+        constexpr uint32_t idesc_narrow =
+            F8 ? idesc_e4m3_f32(PAIR_M, BN / 2) : idesc_bf16_f32(PAIR_M, BN / 2, 0, B_MN_MAJOR ? 1 : 0);
         int s = 0;
         uint32_t ph = 0;
         int it = 0;
@@ -265,7 +273,10 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_const
                         const uint64_t bd =
                             B_MN_MAJOR ? smem_desc_sw128(b_addr + at * ATOM_B + kk * 16 * 128, 64 * BK * 2, 1024)
                                        : smem_desc_sw128(b_addr + at * ATOM_B + kk * 32, 16, 1024);
-                        umma_bf16_pair(dtm, ad, bd, idesc, (kb | at | kk) != 0 ? 1u : 0u);
+                        if constexpr (F8)
+                            umma_e4m3_pair(dtm, ad, bd, idesc, (kb | at | kk) != 0 ? 1u : 0u);
+                        else
+                            umma_bf16_pair(dtm, ad, bd, idesc, (kb | at | kk) != 0 ? 1u : 0u);
                     }
                 }
                 umma_commit_pair_multicast(&empty[s], MC ? 0xF : 0x3);
@@ -435,11 +446,11 @@ int resident_pairs(const void* kern, int threads, int* out, int cluster = 2) {
 
 // With MC, `tiles` holds units of two tiles (num_tiles units) and the grid is
 // made of clusters of four CTAs (two pairs).
-template <bool B_MN, class Epi, bool RING = false, bool MC = false>
+template <bool B_MN, class Epi, bool RING = false, bool MC = false, bool F8 = false>
 int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, const int2* tiles, int num_tiles,
                      const Epi& epi, int32_t* status, cudaStream_t st, const tc::RingArgs& ring = tc::RingArgs{}) {
     using namespace tc2;
-    auto kern = tc_gemm_pair_kernel<B_MN, Epi, RING, MC>;
+    auto kern = tc_gemm_pair_kernel<B_MN, Epi, RING, MC, F8>;
     const int threads = threads_of(RING);
     constexpr int cluster = MC ? 4 : 2;
     cudaLaunchConfig_t cfg;
@@ -457,6 +468,7 @@ int launch_pair_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int nkb, cons
     cfg.gridDim = dim3(cluster * clusters);
     const char* name = Epi::kName;
     if constexpr (RING) name = Epi::kRingName;
+    if constexpr (F8) name = Epi::kF8Name;
     {
         KernelScope ks_(name, st);
         SOS_CUDA(cudaLaunchKernelEx(&cfg, kern, mA, mB, nkb, tiles, num_tiles, epi, status, ring));
@@ -595,27 +607,48 @@ int launch_tc_adjoint_pair(const sos_plan_s* p, const void* h16, const void* a16
                                   status, st);
 }
 
-int launch_tc_slices_pair(const sos_plan_s* p, const void* S, int64_t NP, const int2* tiles, int num_tiles,
-                          const int32_t* ex, double* c, int32_t* status, cudaStream_t st) {
+// Tensor maps of the stacked slices: bf16 rows of 64-element atoms, or E4M3
+// bytes of 128-element atoms (128 bytes either way); nkb = K blocks of one row.
+static int slice_maps(const sos_plan_s* p, const SliceFormat& f, const void* S, int64_t NP, CUtensorMap* mA,
+                      CUtensorMap* mB, int* nkb) {
     using namespace tc2;
-    CUtensorMap mA, mB;
-    const int64_t rows = (int64_t)kMaxSlices * NP;
-    SOS_CHECK(make_bf16_map(&mA, S, p->r, rows, p->ld16, BK, BM));
-    SOS_CHECK(make_bf16_map(&mB, S, p->r, rows, p->ld16, BK, BN / 2));
-    tc::SliceSumEpilogue epi{(int)p->N, (int)NP, p->dev.idx, p->ld_idx, c, ex};
-    return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), tiles, num_tiles, epi, status, st);
+    const int64_t rows = (int64_t)f.max_slices * NP;
+    if (f.fp8) {
+        SOS_CHECK(make_u8_map(mA, S, p->r, rows, f.ld, 2 * BK, BM));
+        SOS_CHECK(make_u8_map(mB, S, p->r, rows, f.ld, 2 * BK, BN / 2));
+        *nkb = (int)ceil_div(p->r, 2 * BK);
+    } else {
+        SOS_CHECK(make_bf16_map(mA, S, p->r, rows, f.ld, BK, BM));
+        SOS_CHECK(make_bf16_map(mB, S, p->r, rows, f.ld, BK, BN / 2));
+        *nkb = (int)ceil_div(p->r, BK);
+    }
+    return SOS_OK;
 }
 
-int launch_tc_slice_groups_pair(const sos_plan_s* p, const void* S, int64_t NP, const int2* tiles, int num_tiles,
-                                const void* groups, const int32_t* ex, double* c, int32_t* status, cudaStream_t st) {
-    using namespace tc2;
+int launch_tc_slices_pair(const sos_plan_s* p, const SliceFormat& f, const void* S, int64_t NP, const int2* tiles,
+                          int num_tiles, const int32_t* ex, double* c, int32_t* status, cudaStream_t st) {
     CUtensorMap mA, mB;
-    const int64_t rows = (int64_t)kMaxSlices * NP;
-    SOS_CHECK(make_bf16_map(&mA, S, p->r, rows, p->ld16, BK, BM));
-    SOS_CHECK(make_bf16_map(&mB, S, p->r, rows, p->ld16, BK, BN / 2));
+    int nkb = 0;
+    SOS_CHECK(slice_maps(p, f, S, NP, &mA, &mB, &nkb));
+    tc::SliceSumEpilogue epi{(int)p->N, (int)NP, p->dev.idx, p->ld_idx, c, ex, f.bits};
+    if (f.fp8)
+        return launch_pair_gemm<false, tc::SliceSumEpilogue, false, false, true>(mA, mB, nkb, tiles, num_tiles, epi,
+                                                                                  status, st);
+    return launch_pair_gemm<false>(mA, mB, nkb, tiles, num_tiles, epi, status, st);
+}
+
+int launch_tc_slice_groups_pair(const sos_plan_s* p, const SliceFormat& f, const void* S, int64_t NP,
+                                const int2* tiles, int num_tiles, const void* groups, const int32_t* ex, double* c,
+                                int32_t* status, cudaStream_t st) {
+    CUtensorMap mA, mB;
+    int nkb = 0;
+    SOS_CHECK(slice_maps(p, f, S, NP, &mA, &mB, &nkb));
     tc::SliceGroupEpilogue epi{(int)p->N, (int)NP, (int)(NP / 256), p->dev.idx, p->ld_idx, c, ex,
-                               static_cast<const SliceGroup*>(groups)};
-    return launch_pair_gemm<false>(mA, mB, (int)ceil_div(p->r, BK), tiles, num_tiles, epi, status, st);
+                               static_cast<const SliceGroup*>(groups), f.bits};
+    if (f.fp8)
+        return launch_pair_gemm<false, tc::SliceGroupEpilogue, false, false, true>(mA, mB, nkb, tiles, num_tiles,
+                                                                                    epi, status, st);
+    return launch_pair_gemm<false>(mA, mB, nkb, tiles, num_tiles, epi, status, st);
 }
 
 int diag_gemm_pair(int b_mn_major, const void* X, const void* Y, float* D, int64_t m, int64_t n, int64_t k,

@@ -99,7 +99,8 @@ Workspace workspace_layout(const sos_plan_s* p, int prec) {
         w.a16 = take((size_t)p->N * (size_t)p->ld16 * 2);
         w.h16 = take((size_t)p->N * (size_t)p->ld16h * 2);
         w.resid32 = take((size_t)p->M * 4);
-        w.slices = take((size_t)kMaxSlices * (size_t)round_up(p->N, 256) * (size_t)p->ld16 * 2);
+        const SliceFormat f = slice_format(p);
+        w.slices = take((size_t)f.max_slices * (size_t)round_up(p->N, 256) * (size_t)f.ld * f.elem_bytes);
         w.ex = take((size_t)p->N * 4);
     }
     w.total = off;
@@ -371,6 +372,29 @@ bool use_exact_diag() {
         return e && e[0] == '1';
     }();
     return v;
+}
+
+bool use_slice_fp8() {
+    static const bool v = [] {
+        const char* e = std::getenv("SOS_SLICE_FP8");
+        return e && e[0] == '1';
+    }();
+    return v;
+}
+
+SliceFormat slice_format(const sos_plan_s* p) {
+    SliceFormat f;
+    if (use_slice_fp8()) {
+        f.fp8 = true;
+        f.bits = 4;
+        f.dmax = 15;
+        f.max_slices = kMaxSlices8;
+        f.ld = round_up(p->r, 16);      // bytes: TMA wants 16-byte row strides
+        f.elem_bytes = 1;
+    } else {
+        f.ld = p->ld16;
+    }
+    return f;
 }
 
 bool use_h_ring() {

@@ -113,9 +113,9 @@ int sos_solve(sos_plan_t p, const double* p64, double* A, const sos_solve_opts* 
     auto rel_of = [&](double l) { return std::sqrt(2.0 * std::max(l, 0.0) / pp); };
     out->rel_start_fp64 = rel_of(host[0]);
 
-    // the SOS_FP64_TC stage needs exact slice products (r 31^2 < 2^24) and the
+    // the SOS_FP64_TC stage needs exact slice products (r dmax^2 < 2^24) and the
     // CTA-pair kernels; without them the CUDA-core stages run instead
-    const bool tc = o->tc_fp64 && p->r * 31 * 31 < ((int64_t)1 << 24) && use_cta_pairs();
+    const bool tc = o->tc_fp64 && slice_format(p).exact_for(p->r) && use_cta_pairs();
     int prec = o->start_prec == SOS_FP64 ? SOS_FP32 : o->start_prec;
     sos_state s{A32, m32, v32, 0, 0, 0};
     double best = INFINITY, last_gain = INFINITY;

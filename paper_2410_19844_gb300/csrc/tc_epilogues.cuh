@@ -13,6 +13,9 @@ namespace sos {
 // Tensor map of a bf16 matrix (kernels_tc.cu).
 int make_bf16_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld,
                   uint32_t box_inner, uint32_t box_outer);
+// Tensor map of a uint8 matrix (kernels_tc.cu): inner and ld in bytes.
+int make_u8_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_inner,
+                uint32_t box_outer);
 int diag_gemm_pair(int b_mn_major, const void* X, const void* Y, float* D, int64_t m, int64_t n, int64_t k,
                    int64_t ldx, int64_t ldy, const int2* tiles, int num_tiles, int32_t* status, cudaStream_t st);
 
@@ -90,18 +93,20 @@ __device__ __forceinline__ double pow2_int(int e) {
 // i * NP .. i * NP + N - 1, NP a multiple of 256), so one launch runs every
 // slice pair: a tile at stacked rows (i * NP + a, j * NP + b) is the product of
 // slices i and j.  acc is that product, exact in FP32 (every partial sum is an
-// integer below 2^24); scaled by 2^(ex[a] + ex[b] - 5 (i + j + 2)) it is an
+// integer below 2^24); scaled by 2^(ex[a] + ex[b] - bits (i + j + 2)) it is an
 // exact FP64 value, summed into the FP64 coefficients.  Diagonal pairs (i = j)
 // cover the upper triangle with weights 1 (a = b) and 2 (a < b); cross pairs
 // (i < j) cover every ordered (a, b) with weight 2, which also counts (j, i).
 struct SliceSumEpilogue {
     static constexpr const char* kName = "tc_slices";
+    static constexpr const char* kF8Name = "tc_slices_e4m3";
     static constexpr bool kSegmented = false;
     int N, NP;
     const int32_t* idx;
     int64_t ld_idx;
     double* c;
     const int32_t* ex;
+    int bits = 5;         // bits per slice: 5 (bf16 slices) or 4 (E4M3 slices)
 
     __device__ __forceinline__ void operator()(int a0, int b0, const float* stage, int lane) const {
         const int si = a0 / NP, sj = b0 / NP;
@@ -111,7 +116,7 @@ struct SliceSumEpilogue {
         if (!full && bl + 31 < al) return;
         const int b = bl + lane;
         if (b >= N) return;
-        const int eb = ex[b] - 5 * (si + sj + 2);
+        const int eb = ex[b] - bits * (si + sj + 2);
         const int32_t* col = idx + (int64_t)al * ld_idx + b;
         int32_t g[32];
 #pragma unroll
@@ -140,6 +145,7 @@ struct SliceSumEpilogue {
 // products.  Tiles are (g * TP + I, J), g the group.
 struct SliceGroupEpilogue {
     static constexpr const char* kName = "tc_slices";
+    static constexpr const char* kF8Name = "tc_slices_e4m3";
     static constexpr bool kSegmented = true;
     int N, NP, TP;
     const int32_t* idx;
@@ -147,6 +153,7 @@ struct SliceGroupEpilogue {
     double* c;
     const int32_t* ex;
     const SliceGroup* groups;
+    int bits = 5;         // bits per slice: 5 (bf16 slices) or 4 (E4M3 slices)
 
     __device__ __forceinline__ int segments(int2 tile) const { return groups[tile.x / TP].nseg; }
     // first stacked row of the pair tile in the segment's A and B operands
@@ -164,7 +171,7 @@ struct SliceGroupEpilogue {
         if (al >= N || b0 >= N || b0 + 31 < al) return;
         const int b = b0 + lane;
         if (b >= N) return;
-        const int eb = ex[b] - 5 * (groups[g].order + 2);
+        const int eb = ex[b] - bits * (groups[g].order + 2);
         const int32_t* col = idx + (int64_t)al * ld_idx + b;
         int32_t gi[32];
 #pragma unroll

@@ -10,8 +10,8 @@ arithmetic of the kernel it checks and computed with the oracle.
         |dh_b| <= |dc| + u_r (|h_b| + |dc|)
         |dg_k| <= 2 sum_b |dh_b| |A_bk| + 2 N u sum_b (|h_b| + |dh_b|) |A_bk|
   * coeffs_ref: sampled coefficients c_g and |c|_g, one at a time.
-  * slice_scale_bound: SOS_FP64_TC with s slices -- every term A_ak A_bk is
-    off by at most (s + 2) 2^(-5 s) 2^(e_a + e_b), e_a the exponent of row
+  * slice_scale_bound: SOS_FP64_TC with s slices of b-bit digits -- every
+    term A_ak A_bk is off by at most (s + 2) 2^(-b s) 2^(e_a + e_b), e_a the exponent of row
     a's largest entry; summed over the pairs of each coefficient that is the
     coefficient of the matrix whose row a is 2^e_a everywhere.
 """
@@ -46,7 +46,8 @@ def row_scales(A):
     return np.repeat(np.exp2(e)[:, None], A.shape[1], axis=1)
 
 
-def slice_scale_bound(o, A, slices=8):
-    """(s + 2) 2^(-5 s) times the coefficients of row_scales(A): the bound on
-    every coefficient of the SOS_FP64_TC forward with s slices."""
-    return (slices + 2) * 2.0 ** (-5 * slices) * o.coeffs(row_scales(A))
+def slice_scale_bound(o, A, slices=8, bits=5):
+    """(s + 2) 2^(-b s) times the coefficients of row_scales(A): the bound on
+    every coefficient of the SOS_FP64_TC forward with s slices of b-bit digits
+    (b = 5 in bf16, 4 in E4M3)."""
+    return (slices + 2) * 2.0 ** (-bits * slices) * o.coeffs(row_scales(A))
