@@ -106,3 +106,27 @@ def test_host_calls_validate_arguments():
         L.sos_loss_grad(pl.handle, L.SOS_FP32, 0, 0, 0, 0, 0, 0)   # NULL A: rejected on the host
     with pytest.raises(L.SOSError):
         L.sos_plan_device_idx(pl.handle, 8, 5, 0)                 # rows beyond N: rejected on the host
+
+
+def test_e4m3_slices_change_the_fp64_tc_workspace():
+    """With SOS_SLICE_FP8=1 (read once per process, hence child processes) the
+    SOS_FP64_TC workspace holds 10 byte-wide slice matrices with rows padded to
+    16 bytes instead of 8 bf16 ones with rows padded to 64 elements; nothing
+    else in it changes."""
+    import subprocess
+    import sys
+    code = ("from paper_2410_19844_gb300 import _lib as L\n"
+            "from paper_2410_19844_gb300.engine import Plan\n"
+            "pl = Plan(2, 4, 1000)\n"
+            "print(L.sos_workspace_size(pl.handle, L.SOS_FP64_TC))\n")
+    sizes = {}
+    for fp8 in ("0", "1"):
+        env = dict(os.environ, SOS_SLICE_FP8=fp8, PYTHONPATH=ROOT)
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr
+        sizes[fp8] = int(out.stdout.split()[-1])
+    NP = 256                                     # N = 6 rows, padded to a 256-row tile
+    bf16_slices = 8 * NP * 1024 * 2              # r = 1000: 1024 bf16 per row
+    e4m3_slices = 10 * NP * 1008                 # 1008 bytes per row
+    assert sizes["1"] - sizes["0"] == e4m3_slices - bf16_slices
