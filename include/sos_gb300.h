@@ -68,11 +68,12 @@ typedef enum {
  * scaled and summed in FP64.  With s slices (sos_step_opts.slices, 8 by
  * default) each term A[a][k] A[b][k] is off by at most (s + 2) 2^(-5 s)
  * 2^(e_a + e_b), e_a the exponent of row a's largest entry: about 1e-11 of
- * the rows' scales for 8 slices.  With the environment variable
- * SOS_SLICE_FP8=1 (read once per process) the slices are 4-bit digits held
- * exactly in E4M3 bytes instead, s' = ceil(5 s / 4) of them, exact while
- * r * 15^2 < 2^24 (r <= 74,565), each term off by at most (s' + 2) 2^(-4 s')
- * 2^(e_a + e_b).  The residual and loss are FP64; the adjoint
+ * the rows' scales for 8 slices.  Plans with 17,458 < r <= 74,565 use
+ * slices of 4-bit digits held exactly in E4M3 bytes instead, s' =
+ * ceil(5 s / 4) of them, exact while r * 15^2 < 2^24, each term off by at
+ * most (s' + 2) 2^(-4 s') 2^(e_a + e_b); the environment variable
+ * SOS_SLICE_FP8 (read once per process) forces E4M3 slices (1) or bf16
+ * slices (0) for every plan.  The residual and loss are FP64; the adjoint
  * runs on tensor cores from bf16 H(r) and bf16 A (its error is proportional
  * to the residual, so iterations still converge to the exact fit); the update
  * subtracts an FP32 step from the FP64 iterate, and the optimiser's moments m
@@ -331,8 +332,9 @@ typedef struct {
                                  1% gain), with slices chosen from the current
                                  residual so the forward stays about 2^-10 of it;
                                  the certificate is still the CUDA-core FP64
-                                 evaluation.  Plans with r > 17,458 (or with the
-                                 CTA-pair kernels switched off) take the CUDA-core
+                                 evaluation.  Plans with r > 74,565 (r > 17,458
+                                 with SOS_SLICE_FP8=0), or with the CTA-pair
+                                 kernels switched off, take the CUDA-core
                                  stages.  0: always the CUDA-core stages */
 } sos_solve_opts;
 

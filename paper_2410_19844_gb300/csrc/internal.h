@@ -197,10 +197,13 @@ bool use_mcast();
 // accumulator, which truncates once per 16-deep step (environment variable
 // SOS_EXACT_DIAG = 1, read once; off by default).
 bool use_exact_diag();
-// Whether SOS_FP64_TC slices A into E4M3 bytes of 4-bit digits instead of
-// bf16 5-bit digits (environment variable SOS_SLICE_FP8 = 1, read once).
-bool use_slice_fp8();
-// The slice format of SOS_FP64_TC for this plan.
+// The SOS_FP64_TC slice format the environment asks for (SOS_SLICE_FP8, read
+// once): 1 E4M3 bytes of 4-bit digits, 0 bf16 5-bit digits, -1 (unset) chosen
+// per plan.
+int slice_fp8_setting();
+// The slice format of SOS_FP64_TC for this plan: the one SOS_SLICE_FP8 names,
+// else bf16 slices where their products are exact (r <= 17,458) and E4M3
+// slices above (they are exact up to r = 74,565).
 SliceFormat slice_format(const sos_plan_s* plan);
 // Row-block band height of the adjoint's tile list (SOS_BAND_ADJ, default 8).
 int adjoint_band();

@@ -374,17 +374,20 @@ bool use_exact_diag() {
     return v;
 }
 
-bool use_slice_fp8() {
-    static const bool v = [] {
+int slice_fp8_setting() {
+    static const int v = [] {
         const char* e = std::getenv("SOS_SLICE_FP8");
-        return e && e[0] == '1';
+        if (!e || !e[0]) return -1;
+        return e[0] == '1' ? 1 : 0;
     }();
     return v;
 }
 
 SliceFormat slice_format(const sos_plan_s* p) {
     SliceFormat f;
-    if (use_slice_fp8()) {
+    const int want = slice_fp8_setting();
+    const bool bf16_exact = p->r * 31 * 31 < ((int64_t)1 << 24);
+    if (want == 1 || (want < 0 && !bf16_exact)) {
         f.fp8 = true;
         f.bits = 4;
         f.dmax = 15;

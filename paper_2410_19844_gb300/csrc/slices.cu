@@ -316,7 +316,8 @@ int forward_tc64(sos_plan_s* p, const double* A, void* ws, double* c, int slices
     const SliceFormat f = slice_format(p);
     if (!f.exact_for(p->r))
         return fail(SOS_E_UNSUPPORTED, f.fp8 ? "SOS_FP64_TC: r too large for exact E4M3 slice products (r <= 74565)"
-                                             : "SOS_FP64_TC: r too large for exact slice products (r <= 17458)");
+                                             : "SOS_FP64_TC: r too large for exact bf16 slice products (r <= 17458; "
+                                               "SOS_SLICE_FP8=0 forbids the E4M3 slices that reach 74565)");
     const int sf = f.slices_for(slices);     // slices of this format with the bits of `slices` 5-bit ones
     const int64_t NP = round_up(p->N, 256);
     if ((int64_t)f.max_slices * NP > INT32_MAX / 2) return fail(SOS_E_UNSUPPORTED, "SOS_FP64_TC: N too large");

@@ -11,10 +11,15 @@ product), through the C ABI, against the oracle.
     >= s) add at most s 2^(-5 s) 2^(e_a + e_b) and the truncated tails of the
     two rows 2 2^(-5 s) 2^(e_a + e_b); the FP64 sums add rounding far below.
   * Fewer slices: the loss error shrinks about 32-fold per slice.
+  * Past r = 17,458, where bf16 slice products would not be exact, the plan
+    takes E4M3 slices of 4-bit digits (exact up to r = 74,565); r = 74,566 is
+    refused.
   * The adjoint reads bf16 H(r) and bf16 A: inside (2^-7 + 4 N 2^-24) 2|H(r)||A|.
   * Steps converge: the solver with tc_fp64 certifies an SOS target below
     1e-8, the oracle agreeing.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -53,12 +58,13 @@ def test_tc_gemm_is_exact_on_small_integers(k, pairs):
     assert np.array_equal(D.cpu().numpy().astype(np.int64), ref)
 
 
-def scale_bound(o, A, slices=8):
-    """(s + 2) 2^(-5 s) times the coefficients of the matrix whose row a is
-    2^e_a everywhere (e_a: exponent of the row's largest entry, frexp)."""
+def scale_bound(o, A, slices=8, bits=5):
+    """(s + 2) 2^(-b s) times the coefficients of the matrix whose row a is
+    2^e_a everywhere (e_a: exponent of the row's largest entry, frexp), for s
+    slices of b-bit digits."""
     e = np.frexp(np.abs(A).max(axis=1))[1].astype(np.float64)
     E = np.repeat(np.exp2(e)[:, None], A.shape[1], axis=1)
-    return (slices + 2) * 2.0 ** (-5 * slices) * o.coeffs(E), E
+    return (slices + 2) * 2.0 ** (-bits * slices) * o.coeffs(E), E
 
 
 def problem(n, two_d, r, seed=0, sigma=0.3, spread=True):
@@ -132,12 +138,33 @@ def test_solver_with_tc_fp64_certifies():
 
 
 def test_fp64_tc_rejects_what_it_cannot_do_exactly():
-    pl = Plan(2, 4, 17459)                     # r 31^2 >= 2^24
-    A = torch.zeros(pl.N, 17459, dtype=torch.float64, device=DEV)
+    pl = Plan(2, 4, 74566)                     # r 15^2 >= 2^24: neither slice format is exact
+    A = torch.zeros(pl.N, 74566, dtype=torch.float64, device=DEV)
     with pytest.raises(L.SOSError):
         pl.coeffs(A, "fp64_tc")
     with pytest.raises(L.SOSError):
         L.sos_loss_grad_batched(pl.handle, L.SOS_FP64_TC, 1, 0, 0, 0, 0, 0, 0)
+
+
+@pytest.mark.parametrize("r", [17459, 30000])
+def test_fp64_tc_past_the_bf16_limit_takes_e4m3_slices(r):
+    """r 31^2 >= 2^24: bf16 slice products would not be exact, so the plan takes
+    E4M3 slices of 4-bit digits (10 for the default 8 five-bit ones), inside
+    their bound (s' + 2) 2^(-4 s') per term (the default process, SOS_SLICE_FP8
+    unset, unless the environment forces a format)."""
+    if os.environ.get("SOS_SLICE_FP8"):
+        pytest.skip("SOS_SLICE_FP8 forces one format for every plan")
+    o, A, _ = problem(2, 4, r)
+    pl = Plan(2, 4, r)
+    L.sos_timing_reset()
+    L.sos_timing_enable(True)
+    c = pl.coeffs(torch.from_numpy(A).to(DEV), "fp64_tc").cpu().numpy()
+    torch.cuda.synchronize()
+    L.sos_timing_enable(False)
+    assert "tc_slices_e4m3" in L.sos_timing_report()
+    c_ref = o.coeffs(A)
+    bound, _ = scale_bound(o, A, slices=10, bits=4)
+    assert np.all(np.abs(c - c_ref) <= bound + 1e-15 * o.coeffs(np.abs(A)))
 
 
 def test_fp64_tc_nonfinite_entry_sets_status():
