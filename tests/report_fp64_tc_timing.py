@@ -17,7 +17,11 @@ With --gemm-peaks the report first times cuBLAS GEMMs of 8192^3 in bf16
 (torch.matmul) and E4M3 (torch._scaled_mm, bf16 output): 10 calls as a burst,
 then about 4 s of calls, with the clocks and power of the long run.
 
-    [SOS_SLICE_FP8=1] python tests/report_fp64_tc_timing.py [--gemm-peaks] [--out FILE]
+    [SOS_SLICE_FP8=1|0] python tests/report_fp64_tc_timing.py [--gemm-peaks] [--workloads a,b] [--out FILE]
+
+--workloads picks from quartic100 (n = 99, 2d = 4, N = 5050), n10 (n = 10,
+2d = 10, N = 3003), medium (n = 18, 2d = 8, N = 7315) and large (n = 20,
+2d = 8, N = 10,626); the default is quartic100,large.
 """
 import argparse
 import json
@@ -130,22 +134,26 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
     ap.add_argument("--gemm-peaks", action="store_true")
+    ap.add_argument("--workloads", default="quartic100,large")
     args = ap.parse_args()
     pk, kind = peak()
-    fp8 = os.environ.get("SOS_SLICE_FP8") == "1"
+    fp8 = os.environ.get("SOS_SLICE_FP8") == "1"      # unset: bf16 slices at every size here (r <= 17,458)
     if fp8:
         pk, kind = 2 * pk, kind + " bf16 x 2"
     fmt = "E4M3 4-bit" if fp8 else "bf16 5-bit"
     lines = [f"# One SOS_FP64_TC step, per kernel ({fmt} slices)", "",
              "Command: " + ("SOS_SLICE_FP8=1 " if fp8 else "") + "python tests/report_fp64_tc_timing.py"
-             + (" --gemm-peaks" if args.gemm_peaks else ""), ""]
+             + (" --gemm-peaks" if args.gemm_peaks else "")
+             + (f" --workloads {args.workloads}" if args.workloads != "quartic100,large" else ""), ""]
     if args.gemm_peaks:
         gemm_peaks(lines)
     lines += [f"tensor peak for the slice products: {pk:.0f} TFLOP/s ({kind}).", "",
               "| workload | N = r | slices | step ms | slice products ms | products TFLOP/s | of peak "
               "| clocks (median SM, power, reasons) | CUDA-core FP64 forward ms | kernels (ms per step) |",
               "|---|---|---|---|---|---|---|---|---|---|"]
-    for name, n, two_d in (("quartic n=100", 99, 4), ("large n=20 2d=8", 20, 8)):
+    known = {"quartic100": ("quartic n=100", 99, 4), "n10": ("n=10 2d=10", 10, 10),
+             "medium": ("medium n=18 2d=8", 18, 8), "large": ("large n=20 2d=8", 20, 8)}
+    for name, n, two_d in (known[k] for k in args.workloads.split(",")):
         pl = Plan(n, two_d)
         N = pl.N
         A = torch.from_numpy(sos_inputs.normal_matrix(N, N, 1, sigma=0.1)).cuda()
