@@ -59,12 +59,23 @@ struct Item {
 
 // counts[0..2]: forward, residual, adjoint items; items laid out as three
 // arrays of `cap` entries.
+//
+// The forward and the adjoint run 128 threads per 64 x 64 tile: thread (tx, ty),
+// tx = 0..15 and ty = 0..7, owns rows 8 ty .. 8 ty + 7 and columns 4 tx .. 4 tx
+// + 3, so each 16-deep step reads 8 + 4 staged values (three 16-byte shared
+// loads) for 32 multiply-adds.  The values of the next step (and, for the
+// adjoint, the index entries of the step after) are loaded into registers
+// while the current step computes.  Every entry of the tile still accumulates
+// its products one k at a time in increasing k, as one fused multiply-add each.
+constexpr int kT2 = 128;
+constexpr int kHP = 68;       // staged row length: 64 + 4 keeps rows 16-byte aligned and spreads the stores
+
 template <typename T>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT2)
 group_forward(const int* __restrict__ counts, const Item* __restrict__ items, const Inst<T>* __restrict__ insts,
               const long long* __restrict__ step) {
-    __shared__ T As[16][65];      // padded: staged with k fastest across threads
-    __shared__ T Bs[16][65];
+    __shared__ __align__(16) T As[16][kHP];     // [k][row of the tile]
+    __shared__ __align__(16) T Bs[16][kHP];     // [k][column of the tile]
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int n_items = counts[0];
     const long long now = *step;
@@ -74,41 +85,53 @@ group_forward(const int* __restrict__ counts, const Item* __restrict__ items, co
         const int N = in.N, r = in.r;
         const T* A = ((now - in.join) & 1) ? in.A1 : in.A0;
         const int row0 = it.i * 64, col0 = it.j * 64;
-        T acc[4][4];
+        T acc[8][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        // staged element l of this thread: k = k0 + (e & 15), tile row or column e >> 4, e = tid + 128 l
+        T ra[8], rb[8];
+        auto load = [&](int k0) {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const int e = tid + l * kT2, kk = e & 15, rr = e >> 4;
+                const int gk = k0 + kk, ga = row0 + rr, gb = col0 + rr;
+                ra[l] = (ga < N && gk < r) ? A[(int64_t)ga * r + gk] : T(0);
+                rb[l] = (gb < N && gk < r) ? A[(int64_t)gb * r + gk] : T(0);
+            }
+        };
+        load(0);
         for (int k0 = 0; k0 < r; k0 += 16) {
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const int e = tid + l * kT, rr = e >> 4, kk = e & 15;
-                const int gk = k0 + kk, ga = row0 + rr, gb = col0 + rr;
-                As[kk][rr] = (ga < N && gk < r) ? A[(int64_t)ga * r + gk] : T(0);
-                Bs[kk][rr] = (gb < N && gk < r) ? A[(int64_t)gb * r + gk] : T(0);
+            for (int l = 0; l < 8; ++l) {
+                const int e = tid + l * kT2, kk = e & 15, rr = e >> 4;
+                As[kk][rr] = ra[l];
+                Bs[kk][rr] = rb[l];
             }
             __syncthreads();
+            if (k0 + 16 < r) load(k0 + 16);
 #pragma unroll
             for (int kk = 0; kk < 16; ++kk) {
-                T a[4], b[4];
+                T a[8], b[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+                for (int i = 0; i < 8; ++i) a[i] = As[kk][8 * ty + i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][4 * tx + j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int a = row0 + ty + 16 * i;
+        for (int i = 0; i < 8; ++i) {
+            const int a = row0 + 8 * ty + i;
             if (a >= N) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int b = col0 + tx + 16 * j;
+                const int b = col0 + 4 * tx + j;
                 if (b < N) in.G[(int64_t)a * N + b] = acc[i][j];
             }
         }
@@ -253,14 +276,16 @@ group_residual(const int* __restrict__ counts, const Item* __restrict__ items, i
 
 // Tc is the type of the contraction (T, or float for an FP64 group that
 // takes its gradient from the FP64 residual in FP32 arithmetic); the update
-// and the iterate stay in T.
+// and the iterate stay in T.  H is gathered from the residual through the
+// index table: the table entries two steps ahead and the gathered values and
+// A one step ahead are in registers while a step computes.
 template <typename T, typename Tc, typename U = T>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT2)
 group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, int cap,
               const Inst<T>* __restrict__ insts, const long long* __restrict__ step, int optimizer, double b1,
               double b2, double eps) {
-    __shared__ Tc Hs[16][65];     // padded: staged with b fastest across threads
-    __shared__ Tc Bs[16][64];
+    __shared__ __align__(16) Tc Hs[16][kHP];    // [b][row a of the tile]
+    __shared__ __align__(16) Tc Bs[16][kHP];    // [b][column k of the tile]
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int n_items = counts[2];
     const long long now = *step - 1;     // the residual kernel has advanced the counter
@@ -272,36 +297,59 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
         const T* A = (taken & 1) ? in.A1 : in.A0;
         T* A_next = (taken & 1) ? in.A0 : in.A1;
         const int row0 = it.i * 64, col0 = it.j * 64;
-        Tc acc[4][4];
+        Tc acc[8][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = Tc(0);
+        // staged element l, e = tid + 128 l: H entry (row0 + (e >> 4), b0 + (e & 15)),
+        // A entry (b0 + (e >> 6), col0 + (e & 63))
+        int ix[8];
+        Tc hv[8], bv[8];
+        auto load_idx = [&](int b0) {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const int e = tid + l * kT2, a = row0 + (e >> 4), b = b0 + (e & 15);
+                ix[l] = (a < N && b < N) ? in.idx[(int64_t)a * in.ld_idx + b] : -1;
+            }
+        };
+        auto gather = [&]() {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) hv[l] = ix[l] >= 0 ? (Tc)in.resid[ix[l]] : Tc(0);
+        };
+        auto load_b = [&](int b0) {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const int e = tid + l * kT2, b = b0 + (e >> 6), k = col0 + (e & 63);
+                bv[l] = (b < N && k < r) ? (Tc)A[(int64_t)b * r + k] : Tc(0);
+            }
+        };
+        load_idx(0);
+        gather();
+        load_b(0);
+        load_idx(16);
         for (int b0 = 0; b0 < N; b0 += 16) {
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const int e = tid + l * kT;
-                {
-                    const int rr = e >> 4, kk = e & 15;
-                    const int a = row0 + rr, b = b0 + kk;
-                    Hs[kk][rr] = (a < N && b < N) ? (Tc)in.resid[in.idx[(int64_t)a * in.ld_idx + b]] : Tc(0);
-                }
-                {
-                    const int kk = e >> 6, cc = e & 63;
-                    const int b = b0 + kk, k = col0 + cc;
-                    Bs[kk][cc] = (b < N && k < r) ? (Tc)A[(int64_t)b * r + k] : Tc(0);
-                }
+            for (int l = 0; l < 8; ++l) {
+                const int e = tid + l * kT2;
+                Hs[e & 15][e >> 4] = hv[l];
+                Bs[e >> 6][e & 63] = bv[l];
             }
             __syncthreads();
+            if (b0 + 16 < N) {
+                gather();                 // the entries of step b0 + 16, loaded one step ago
+                load_b(b0 + 16);
+                load_idx(b0 + 32);
+            }
 #pragma unroll
             for (int kk = 0; kk < 16; ++kk) {
-                Tc a[4], b[4];
+                Tc a[8], b[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = Hs[kk][ty + 16 * i];
+                for (int i = 0; i < 8; ++i) a[i] = Hs[kk][8 * ty + i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][4 * tx + j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
             }
@@ -313,12 +361,12 @@ group_adjoint(const int* __restrict__ counts, const Item* __restrict__ items, in
         const U c1 = (U)(1.0 - pow(b1, t)), c2 = (U)(1.0 - pow(b2, t));
         const U lr = (U)in.lr, B1 = (U)b1, B2 = (U)b2, EPS = (U)eps, one = U(1);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int a = row0 + ty + 16 * i;
+        for (int i = 0; i < 8; ++i) {
+            const int a = row0 + 8 * ty + i;
             if (a >= N) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int k = col0 + tx + 16 * j;
+                const int k = col0 + 4 * tx + j;
                 if (k >= r) continue;
                 const int64_t e = (int64_t)a * r + k;
                 const U g = U(2) * (U)acc[i][j];
@@ -486,9 +534,9 @@ int launch_step(sos_group_s* g, cudaStream_t st) {
             if (g->fast_fp64)
                 group_forward_df<<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
             else
-                group_forward<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
+                group_forward<T><<<2 * g->grid, kT2, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
         } else {
-            group_forward<T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
+            group_forward<T><<<2 * g->grid, kT2, 0, st>>>(g->d_counts, g->d_items, insts, g->d_step);
         }
     }
     {
@@ -497,14 +545,15 @@ int launch_step(sos_group_s* g, cudaStream_t st) {
     }
     {
         KernelScope ks_("group_adjoint", st);
+        const int blocks = 2 * g->grid;
         if (g->fp32_adjoint && g->fast_fp64)
-            group_adjoint<T, float, float><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts,
+            group_adjoint<T, float, float><<<blocks, kT2, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts,
                                                                    g->d_step, g->optimizer, g->b1, g->b2, g->eps);
         else if (g->fp32_adjoint)
-            group_adjoint<T, float><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
+            group_adjoint<T, float><<<blocks, kT2, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
                                                             g->optimizer, g->b1, g->b2, g->eps);
         else
-            group_adjoint<T, T><<<g->grid, kT, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
+            group_adjoint<T, T><<<blocks, kT2, 0, st>>>(g->d_counts, g->d_items, g->item_cap, insts, g->d_step,
                                                         g->optimizer, g->b1, g->b2, g->eps);
     }
     SOS_CUDA(cudaGetLastError());
