@@ -128,6 +128,10 @@ class Server:
         self.launches = 0
         self.losses32 = np.zeros(2 * capacity)
         self.losses64 = np.zeros(2 * capacity)
+        # each group ticks on its own stream, so the FP64 group's tick runs beside
+        # the FP32 group's and beside the host's bookkeeping of FP32 results
+        self.s32 = torch.cuda.Stream()
+        self.s64 = torch.cuda.Stream()
 
     def close(self):
         if self.g32:
@@ -233,7 +237,8 @@ class Server:
         pi = 0
         out: list = []
         t0 = time.perf_counter() if clock_start is None else clock_start
-        st = _stream_handle()
+        cur = torch.cuda.current_stream()
+        h32, h64 = _stream_handle(self.s32), _stream_handle(self.s64)
         while pi < len(pending) or self.active32 or self.active64:
             now = time.perf_counter() - t0
             while pi < len(pending) and pending[pi].arrival_s <= now:
@@ -244,19 +249,21 @@ class Server:
                 if pi < len(pending):
                     time.sleep(max(0.0, min(0.01, pending[pi].arrival_s - now)))
                 continue
-            if self.active32:
-                L.sos_group_sync(self.g32, st)
-                L.sos_group_run(self.g32, self.K, st)
-            if self.active64:
-                L.sos_group_sync(self.g64, st)
-                L.sos_group_run(self.g64, self.K, st)
+            # both ticks follow the admissions and promotions queued on the current stream
+            ran32, ran64 = bool(self.active32), bool(self.active64)
+            if ran32:
+                self.s32.wait_stream(cur)
+                L.sos_group_sync(self.g32, h32)
+                L.sos_group_run(self.g32, self.K, h32)
+            if ran64:
+                self.s64.wait_stream(cur)
+                L.sos_group_sync(self.g64, h64)
+                L.sos_group_run(self.g64, self.K, h64)
             self.ticks += 1
             self.group_steps += self.K
-            self.launches += 4 * self.K * (bool(self.active32) + bool(self.active64))
-            if self.active32:
-                L.sos_group_losses(self.g32, self.losses32.ctypes.data, st)
-            if self.active64:
-                L.sos_group_losses(self.g64, self.losses64.ctypes.data, st)
+            self.launches += 4 * self.K * (ran32 + ran64)
+            if ran32:
+                L.sos_group_losses(self.g32, self.losses32.ctypes.data, h32)    # waits for the FP32 tick only
             now = time.perf_counter() - t0
             for slot, a in list(self.active32.items()):
                 a.steps32 += self.K
@@ -281,6 +288,9 @@ class Server:
                     L.sos_group_set_lr(self.g32, slot, a.lr)
                 elif stalled:
                     self._retire(a, L.SOS_VERDICT_NOT_CONVERGED, rel, now, out)
+            if ran64:
+                L.sos_group_losses(self.g64, self.losses64.ctypes.data, h64)
+                now = time.perf_counter() - t0
             for slot, a in list(self.active64.items()):
                 if a.fresh:                   # promoted during this tick: no FP64 step yet
                     a.fresh = False
