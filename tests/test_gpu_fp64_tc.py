@@ -167,6 +167,35 @@ def test_fp64_tc_past_the_bf16_limit_takes_e4m3_slices(r):
     assert np.all(np.abs(c - c_ref) <= bound + 1e-15 * o.coeffs(np.abs(A)))
 
 
+def extreme_rows(o, r, seed=7):
+    """A with rows the slicing treats specially: all zeros, subnormal entries
+    only, a single entry, entries spanning 1e-200 .. 1, and huge entries."""
+    g = np.random.default_rng(seed)
+    A = g.normal(0.0, 0.3, size=(o.N, r))
+    A[0] = 0.0
+    A[1] = g.integers(-1000, 1000, size=r) * 5e-324          # subnormal (and zero) entries
+    A[2] = 0.0
+    A[2, r // 2] = -0.75
+    A[3] = g.normal(0.0, 1.0, size=r) * 10.0 ** g.uniform(-200, 0, size=r)
+    A[4] *= 1e150
+    return A
+
+
+@pytest.mark.parametrize("n,two_d,r", [(4, 6, 35), (6, 8, 210)])
+def test_fp64_tc_extreme_rows(n, two_d, r):
+    """Zero, subnormal, single-entry, wide-range and huge rows: the forward stays
+    inside the slicing bound (plus a few subnormal units, where FP64 itself
+    rounds products into the subnormal range)."""
+    o = oracle.Oracle(n, two_d)
+    A = extreme_rows(o, r)
+    pl = Plan(n, two_d, r)
+    c = pl.coeffs(torch.from_numpy(A).to(DEV), "fp64_tc").cpu().numpy()
+    c_ref = o.coeffs(A)
+    bound, _ = scale_bound(o, A)
+    assert np.all(np.isfinite(c))
+    assert np.all(np.abs(c - c_ref) <= bound + 1e-15 * o.coeffs(np.abs(A)) + 1e-320)
+
+
 def test_fp64_tc_nonfinite_entry_sets_status():
     """A NaN in A reaches the coefficients (its slices carry NaN) and the status word."""
     o, A, p = problem(4, 6, 35, spread=False)

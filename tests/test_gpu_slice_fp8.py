@@ -56,6 +56,17 @@ for n, two_d, r in [(3, 4, 10), (4, 6, 35), (6, 8, 210), (5, 6, 300), (9, 6, 700
     print("forward", n, two_d, r, "worst error / bound", float(np.max(np.abs(c - c_ref) / (cb + 1e-300))))
     del pl
 
+# rows the slicing treats specially: zeros, subnormals only, one entry, 1e-200 .. 1, huge
+from test_gpu_fp64_tc import extreme_rows
+for n, two_d, r in [(4, 6, 35), (6, 8, 210)]:
+    o = oracle.Oracle(n, two_d)
+    A = extreme_rows(o, r)
+    c = Plan(n, two_d, r).coeffs(torch.from_numpy(A).cuda(), "fp64_tc").cpu().numpy()
+    c_ref = o.coeffs(A)
+    cb = bounds.slice_scale_bound(o, A, slices=10, bits=4)
+    assert np.all(np.isfinite(c)), (n, two_d, r)
+    assert np.all(np.abs(c - c_ref) <= cb + 1e-15 * o.coeffs(np.abs(A)) + 1e-320), (n, two_d, r)
+
 # fewer slices: s 5-bit slices -> ceil(5 s / 4) 4-bit ones, the loss error shrinking accordingly
 o, A, p = problem(6, 8, 210, seed=3, spread=False)
 pl = Plan(6, 8, 210)
