@@ -6,7 +6,7 @@
 // GPU the way a grouped GEMM shares it:
 //   forward   64 x 64 tiles of G = A A^T on or above the diagonal, written
 //             to the problem's G (no atomics)                  (Eq. 1)
-//   residual  chunks of 2048 coefficients: c_g is gathered from G through the
+//   residual  chunks of 512 coefficients: c_g is gathered from G through the
 //             plan's pair lists, r = c - p, partial sums of ||r||^2, ||p||^2;
 //             one thread also advances the group's step counter, which the
 //             forward reads before it and the adjoint (as counter - 1) after it
@@ -31,7 +31,7 @@ namespace sos {
 namespace grp {
 
 constexpr int kT = 256;
-constexpr int kChunk = 2048;
+constexpr int kChunk = 512;
 
 template <typename T>
 struct Inst {
