@@ -327,7 +327,7 @@ def run_serving(args):
     t_plain = time.perf_counter() - t0
     plain_rate = len(sample) / t_plain
 
-    srv = Server(capacity=512, steps_per_tick=32)
+    srv = Server(capacity=1024, steps_per_tick=32)
     srv.run(jobs[:8])                                          # warm-up
     srv_launch0 = srv.launches
     torch.cuda.synchronize()
@@ -358,7 +358,7 @@ def run_serving(args):
             "speedup_vs_plain": served_rate / plain_rate, "verdict_agreement_with_plain": f"{agree}/{len(sample)}",
             "verdicts": counts, "sos_targets_certified": f"{sos_ok}/{(len(jobs) + 1) // 2}",
             "negative_targets_not_converged": f"{neg_ok}/{len(jobs) // 2}",
-            "latency": latency, "slots": 512, "steps_per_tick": 32, "gpu_launches": launches,
+            "latency": latency, "slots": srv.capacity, "steps_per_tick": 32, "gpu_launches": launches,
             "note": "grouped FP32 then FP64 (FP32 adjoint) steps, captured graphs of 32 steps; "
                     "plain = sos_step launches per problem, one problem at a time, same decision rule"}
 
