@@ -130,3 +130,29 @@ def test_e4m3_slices_change_the_fp64_tc_workspace():
     bf16_slices = 8 * NP * 1024 * 2              # r = 1000: 1024 bf16 per row
     e4m3_slices = 10 * NP * 1008                 # 1008 bytes per row
     assert sizes["1"] - sizes["0"] == e4m3_slices - bf16_slices
+
+
+def test_slice_format_is_chosen_per_plan():
+    """With SOS_SLICE_FP8 unset a plan takes bf16 slices where their products
+    are exact (r <= 17,458) and E4M3 slices above: the workspace of the unset
+    case equals the forced bf16 one at r = 1000 and the forced E4M3 one at
+    r = 20,000."""
+    import subprocess
+    import sys
+
+    def size(r, fp8):
+        code = ("from paper_2410_19844_gb300 import _lib as L\n"
+                "from paper_2410_19844_gb300.engine import Plan\n"
+                f"pl = Plan(2, 4, {r})\n"
+                "print(L.sos_workspace_size(pl.handle, L.SOS_FP64_TC))\n")
+        env = dict(os.environ, PYTHONPATH=ROOT)
+        env.pop("SOS_SLICE_FP8", None)
+        if fp8 is not None:
+            env["SOS_SLICE_FP8"] = fp8
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr
+        return int(out.stdout.split()[-1])
+
+    assert size(1000, None) == size(1000, "0") != size(1000, "1")
+    assert size(20000, None) == size(20000, "1") != size(20000, "0")
