@@ -261,7 +261,7 @@ class Server:
                 L.sos_group_run(self.g64, self.K, h64)
             self.ticks += 1
             self.group_steps += self.K
-            self.launches += 4 * self.K * (ran32 + ran64)
+            self.launches += 3 * self.K * (ran32 + ran64)      # forward, residual, adjoint per step
             if ran32:
                 L.sos_group_losses(self.g32, self.losses32.ctypes.data, h32)    # waits for the FP32 tick only
             now = time.perf_counter() - t0
